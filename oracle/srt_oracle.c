@@ -1,0 +1,561 @@
+/*
+ * FP64 CPU oracle for the discrete spherical Radon transform (SRT) with a
+ * cylindrical aperture.  TEST INFRASTRUCTURE ONLY: it is called by tests/,
+ * by __graft_entry__.smoke() and by bench.py's CPU-baseline leg, never by the
+ * product path.  It shares no code, header or table with the CUDA library.
+ *
+ * What it computes (Sec. 2 and Sec. 3.1 of the paper):
+ *   The SRT of f over the shell of radius l centred at sensor r is
+ *     int_0^pi int_0^2pi f(r + l(sin t cos a, sin t sin a, cos t)) l^2 sin t da dt
+ *   (Sec. 2, spherical parametrisation), rewritten as an outer integral over
+ *   t with measure l dt of an in-plane circle integral at radius l sin t with
+ *   measure (l sin t) da (Sec. 2, "bringing a copy of l outside").
+ *   The paper discretises f with piecewise-constant voxels and represents the
+ *   two circular transforms by exact-arc-length matrices on a shared radius
+ *   grid {l_l} (Sec. 3.1, Algorithm 1).  The intermediate f^{1,2} therefore
+ *   lives on (z-slab k, radius bin l) cells and is constant on each cell,
+ *   taking the value of the in-plane circle integral at the bin centre rho_l.
+ *
+ *   This oracle evaluates that discrete operator shell by shell, WITHOUT
+ *   forming either matrix and without the two-stage product:
+ *     p[j,h,m] = sum over t-segments s of  l_m |s|  *  rho_{l(s)} *
+ *                sum over a-segments q of |q| * f(pixel(q), slab(s))
+ *   where the t-breakpoints are the crossings of the semicircle
+ *   (z_h + l_m cos t, l_m sin t) with slab planes and radius-bin edges, and
+ *   the a-breakpoints are the crossings of the circle s_j + rho (cos a, sin a)
+ *   with the pixel grid lines.  Every segment is assigned to the cell holding
+ *   its midpoint (boundary ties have measure zero).
+ *
+ * Readings of the paper used here (its text is silent on them):
+ *   - radii grid shared by rho and l, cell centred: l_l = lo + (l+1/2) dl;
+ *   - radius bins [lo + l dl, lo + (l+1) dl]; parts of a semicircle outside
+ *     [lo, hi] carry no weight (the in-plane integral vanishes below lo and
+ *     the aperture is truncated above hi);
+ *   - sensors phi_j = phi0 + 2 pi j / n_phi, ring heights at cell centres of
+ *     [zs_lo, zs_hi]; voxel centres (i - (M-1)/2) * spacing (box centred at 0);
+ *   - arc lengths in mm, no normalisation.
+ *
+ * Layouts: f[ix][iy][iz] (z fastest), p[j][h][m].  All arithmetic is FP64.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846264338327950288
+
+typedef struct {
+  int32_t ms, mz;        /* voxels: ms x ms x mz                          */
+  double dxy, dz;        /* voxel spacing, mm                              */
+  double radius;         /* cylinder radius R, mm                          */
+  int32_t n_phi;         /* sensor columns                                 */
+  double phi0;           /* angle of column 0, rad                         */
+  int32_t n_zs;          /* sensor rings                                   */
+  double zs_lo, zs_hi;   /* ring heights are cell centres of [lo, hi]      */
+  int32_t n_ell;         /* radius bins shared by rho and l                */
+  double ell_lo, ell_hi; /* radius grid range                              */
+} orc_geom;
+
+/* ---------------------------------------------------------------- helpers */
+
+static int cmp_double(const void* a, const void* b) {
+  double x = *(const double*)a, y = *(const double*)b;
+  return (x > y) - (x < y);
+}
+
+static double wrap_2pi(double a) { return a < 0.0 ? a + 2.0 * ORC_PI : a; }
+
+static double half_x(const orc_geom* g) { return 0.5 * g->ms * g->dxy; }
+static double half_z(const orc_geom* g) { return 0.5 * g->mz * g->dz; }
+static double dell(const orc_geom* g) { return (g->ell_hi - g->ell_lo) / g->n_ell; }
+static double ell_centre(const orc_geom* g, int l) { return g->ell_lo + (l + 0.5) * dell(g); }
+static double ring_z(const orc_geom* g, int h) {
+  return g->zs_lo + (h + 0.5) * (g->zs_hi - g->zs_lo) / g->n_zs;
+}
+static double sensor_x(const orc_geom* g, int j) {
+  return g->radius * cos(g->phi0 + 2.0 * ORC_PI * j / g->n_phi);
+}
+static double sensor_y(const orc_geom* g, int j) {
+  return g->radius * sin(g->phi0 + 2.0 * ORC_PI * j / g->n_phi);
+}
+
+/* Work buffers of one thread. */
+typedef struct {
+  double* tb;   /* t-breakpoints                 */
+  double* ab;   /* a-breakpoints                 */
+  int* cpix;    /* cached circle: pixel index    */
+  double* clen; /* cached circle: arc length     */
+  int cn;       /* cached circle: segment count  */
+  int cl;       /* cached circle: radius bin, -1 */
+} orc_ws;
+
+static int ws_init(orc_ws* w, const orc_geom* g) {
+  int nt = 2 * (g->mz + 1) + 2 * (g->n_ell + 1) + 4;
+  int na = 4 * (g->ms + 1) + 4;
+  w->tb = (double*)malloc(sizeof(double) * nt);
+  w->ab = (double*)malloc(sizeof(double) * na);
+  w->cpix = (int*)malloc(sizeof(int) * na);
+  w->clen = (double*)malloc(sizeof(double) * na);
+  w->cn = 0;
+  w->cl = -1;
+  return (w->tb && w->ab && w->cpix && w->clen) ? 0 : -1;
+}
+
+static void ws_free(orc_ws* w) {
+  free(w->tb);
+  free(w->ab);
+  free(w->cpix);
+  free(w->clen);
+}
+
+/* ------------------------------------------------- in-plane circle walk
+ * Circle centre (sx, sy), radius rho, in the (x, y) plane of the pixel grid.
+ * Breakpoints: every angle where the circle meets a grid line x = const or
+ * y = const.  Each arc between consecutive breakpoints lies in one pixel
+ * (the one holding its midpoint).  Output: (pixel ix*ms+iy, arc length)
+ * for arcs inside the grid.  Returns the number of arcs written.          */
+static int circle_walk(const orc_geom* g, double sx, double sy, double rho, double* ab,
+                       int* pix, double* len) {
+  const double hx = half_x(g);
+  int n = 0;
+  for (int i = 0; i <= g->ms; ++i) {
+    double u = -hx + i * g->dxy - sx; /* x-line offset from centre */
+    if (fabs(u) < rho) {
+      double v = sqrt((rho - u) * (rho + u));
+      ab[n++] = wrap_2pi(atan2(v, u));
+      ab[n++] = wrap_2pi(atan2(-v, u));
+    }
+  }
+  for (int i = 0; i <= g->ms; ++i) {
+    double u = -hx + i * g->dxy - sy; /* y-line offset from centre */
+    if (fabs(u) < rho) {
+      double v = sqrt((rho - u) * (rho + u));
+      ab[n++] = wrap_2pi(atan2(u, v));
+      ab[n++] = wrap_2pi(atan2(u, -v));
+    }
+  }
+  qsort(ab, n, sizeof(double), cmp_double);
+  int out = 0;
+  int nseg = n > 0 ? n : 1;
+  for (int s = 0; s < nseg; ++s) {
+    double a0, a1;
+    if (n == 0) {
+      a0 = 0.0;
+      a1 = 2.0 * ORC_PI;
+    } else {
+      a0 = ab[s];
+      a1 = (s + 1 < n) ? ab[s + 1] : ab[0] + 2.0 * ORC_PI;
+    }
+    if (!(a1 > a0)) continue;
+    double am = 0.5 * (a0 + a1);
+    double x = sx + rho * cos(am), y = sy + rho * sin(am);
+    int ix = (int)floor((x + hx) / g->dxy);
+    int iy = (int)floor((y + hx) / g->dxy);
+    if (ix < 0 || ix >= g->ms || iy < 0 || iy >= g->ms) continue;
+    pix[out] = ix * g->ms + iy;
+    len[out] = rho * (a1 - a0);
+    ++out;
+  }
+  return out;
+}
+
+/* ------------------------------------------------------- shell walk
+ * Shell (j, h, m): sensor (s_j, z_h), radius l_m.  The outer variable t runs
+ * over [0, pi]; the point (z, rho) = (z_h + l_m cos t, l_m sin t) moves on a
+ * semicircle of the (z, rho) half plane.  For every t-segment inside a
+ * (slab k, radius bin l) cell, the in-plane circle of radius rho_l about s_j
+ * is walked through slab k.  emit(ctx, voxel, weight) receives every
+ * elementary contribution; voxel = (ix*ms + iy)*mz + k.                  */
+typedef void (*emit_fn)(void* ctx, long voxel, double weight);
+
+static void shell_walk(const orc_geom* g, orc_ws* w, int j, int h, int m, emit_fn emit,
+                       void* ctx) {
+  const double hz = half_z(g), dl = dell(g);
+  const double ell = ell_centre(g, m), zc = ring_z(g, h);
+  const double sx = sensor_x(g, j), sy = sensor_y(g, j);
+  double* tb = w->tb;
+  int n = 0;
+  tb[n++] = 0.0;
+  tb[n++] = ORC_PI;
+  for (int k = 0; k <= g->mz; ++k) {
+    double u = -hz + k * g->dz - zc; /* slab plane offset */
+    if (fabs(u) < ell) tb[n++] = atan2(sqrt((ell - u) * (ell + u)), u);
+  }
+  for (int l = 0; l <= g->n_ell; ++l) {
+    double rb = g->ell_lo + l * dl; /* radius-bin edge */
+    if (rb > 0.0 && rb < ell) {
+      double a = atan2(rb, sqrt((ell - rb) * (ell + rb)));
+      tb[n++] = a;
+      tb[n++] = ORC_PI - a;
+    }
+  }
+  qsort(tb, n, sizeof(double), cmp_double);
+  w->cl = -1;
+  for (int s = 0; s + 1 < n; ++s) {
+    double t0 = tb[s], t1 = tb[s + 1];
+    if (!(t1 > t0)) continue;
+    double tm = 0.5 * (t0 + t1);
+    double z = zc + ell * cos(tm), rho = ell * sin(tm);
+    int k = (int)floor((z + hz) / g->dz);
+    int l = (int)floor((rho - g->ell_lo) / dl);
+    if (k < 0 || k >= g->mz || l < 0 || l >= g->n_ell) continue;
+    double wt = ell * (t1 - t0); /* arc length in the (z, rho) plane */
+    if (l != w->cl) {            /* in-plane circle for bin l, radius rho_l */
+      w->cn = circle_walk(g, sx, sy, ell_centre(g, l), w->ab, w->cpix, w->clen);
+      w->cl = l;
+    }
+    for (int q = 0; q < w->cn; ++q)
+      emit(ctx, (long)w->cpix[q] * g->mz + k, wt * w->clen[q]);
+  }
+}
+
+/* ------------------------------------------------------- callbacks */
+typedef struct {
+  const double* f;
+  double acc;
+} fwd_ctx;
+static void emit_fwd(void* c, long v, double wgt) {
+  fwd_ctx* x = (fwd_ctx*)c;
+  x->acc += wgt * x->f[v];
+}
+
+typedef struct {
+  double* out;
+  double gval;
+} adj_ctx;
+static void emit_adj(void* c, long v, double wgt) {
+  adj_ctx* x = (adj_ctx*)c;
+  x->out[v] += wgt * x->gval;
+}
+
+typedef struct {
+  long* vox;
+  double* wgt;
+  int n, cap, overflow;
+} list_ctx;
+static void emit_list(void* c, long v, double wgt) {
+  list_ctx* x = (list_ctx*)c;
+  if (x->n < x->cap) {
+    x->vox[x->n] = v;
+    x->wgt[x->n] = wgt;
+    x->n++;
+  } else {
+    x->overflow = 1;
+  }
+}
+
+static int check_geom(const orc_geom* g) {
+  if (!g || g->ms <= 0 || g->mz <= 0 || g->n_phi <= 0 || g->n_zs <= 0 || g->n_ell <= 0) return -1;
+  if (!(g->dxy > 0) || !(g->dz > 0) || !(g->radius > 0) || !(g->ell_hi > g->ell_lo)) return -1;
+  if (!(g->ell_lo > 0)) return -1;
+  if (!(g->zs_hi > g->zs_lo)) return -1;
+  return 0;
+}
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+}
+
+/* ====================================================== exported API */
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Forward on a list of shells: shells[3*i .. 3*i+2] = (j, h, m). */
+int orc_forward_shells(const orc_geom* g, const double* f, const int32_t* shells, long n,
+                       double* out, int nthreads) {
+  if (check_geom(g)) return -1;
+  set_threads(nthreads);
+  int err = 0;
+#pragma omp parallel
+  {
+    orc_ws w;
+    if (ws_init(&w, g)) {
+#pragma omp atomic write
+      err = -2;
+    } else {
+#pragma omp for schedule(dynamic, 8)
+      for (long i = 0; i < n; ++i) {
+        fwd_ctx c = {f, 0.0};
+        shell_walk(g, &w, shells[3 * i], shells[3 * i + 1], shells[3 * i + 2], emit_fwd, &c);
+        out[i] = c.acc;
+      }
+    }
+    ws_free(&w);
+  }
+  return err;
+}
+
+/* Full forward: p[j][h][m]. */
+int orc_forward(const orc_geom* g, const double* f, double* p, int nthreads) {
+  if (check_geom(g)) return -1;
+  long ns = (long)g->n_phi * g->n_zs * g->n_ell;
+  int32_t* sh = (int32_t*)malloc(sizeof(int32_t) * 3 * ns);
+  if (!sh) return -2;
+  long i = 0;
+  for (int j = 0; j < g->n_phi; ++j)
+    for (int h = 0; h < g->n_zs; ++h)
+      for (int m = 0; m < g->n_ell; ++m) {
+        sh[3 * i] = j;
+        sh[3 * i + 1] = h;
+        sh[3 * i + 2] = m;
+        ++i;
+      }
+  int r = orc_forward_shells(g, f, sh, ns, p, nthreads);
+  free(sh);
+  return r;
+}
+
+/* Full adjoint: f'[ix][iy][iz] = sum over shells of weight * p[shell].
+ * Uses the same shell walk (and hence the same weights) as the forward, with
+ * one FP64 accumulation buffer per thread summed in thread order.        */
+int orc_adjoint(const orc_geom* g, const double* p, double* f, int nthreads) {
+  if (check_geom(g)) return -1;
+  set_threads(nthreads);
+  long nv = (long)g->ms * g->ms * g->mz;
+  long ns = (long)g->n_phi * g->n_zs * g->n_ell;
+  int nt = orc_num_threads();
+  double* buf = (double*)calloc((size_t)nt * nv, sizeof(double));
+  if (!buf) return -2;
+  int err = 0;
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    orc_ws w;
+    if (ws_init(&w, g)) {
+#pragma omp atomic write
+      err = -2;
+    } else {
+      adj_ctx c = {buf + (size_t)tid * nv, 0.0};
+#pragma omp for schedule(dynamic, 8)
+      for (long s = 0; s < ns; ++s) {
+        int j = (int)(s / ((long)g->n_zs * g->n_ell));
+        int h = (int)((s / g->n_ell) % g->n_zs);
+        int m = (int)(s % g->n_ell);
+        c.gval = p[s];
+        if (c.gval != 0.0) shell_walk(g, &w, j, h, m, emit_adj, &c);
+      }
+    }
+    ws_free(&w);
+  }
+  for (long v = 0; v < nv; ++v) {
+    double a = 0.0;
+    for (int t = 0; t < nt; ++t) a += buf[(size_t)t * nv + v];
+    f[v] = a;
+  }
+  free(buf);
+  return err;
+}
+
+/* Elementary contributions of one shell: (voxel, weight) pairs as emitted by
+ * the walk (a voxel may appear several times).  Returns the count, or -3 if
+ * cap was too small.                                                       */
+long orc_shell_contrib(const orc_geom* g, int j, int h, int m, long* vox, double* wgt, long cap) {
+  if (check_geom(g)) return -1;
+  orc_ws w;
+  if (ws_init(&w, g)) return -2;
+  list_ctx c = {vox, wgt, 0, (int)cap, 0};
+  shell_walk(g, &w, j, h, m, emit_list, &c);
+  ws_free(&w);
+  return c.overflow ? -3 : c.n;
+}
+
+/* In-plane circle of sensor column j at bin-centre radius rho_l: arcs per
+ * pixel, in walk order (a pixel may appear twice).                        */
+int orc_circle_arcs(const orc_geom* g, int j, int l, int32_t* pix, double* len, int cap) {
+  if (check_geom(g)) return -1;
+  int na = 4 * (g->ms + 1) + 4;
+  if (cap < na) return -3;
+  double* ab = (double*)malloc(sizeof(double) * na);
+  if (!ab) return -2;
+  int* p = (int*)malloc(sizeof(int) * na);
+  int n = circle_walk(g, sensor_x(g, j), sensor_y(g, j), ell_centre(g, l), ab, p, len);
+  for (int i = 0; i < n; ++i) pix[i] = p[i];
+  free(p);
+  free(ab);
+  return n;
+}
+
+/* (z, rho)-plane semicircle of ring h at shell radius l_m: arc length per
+ * (slab k, radius bin l) cell, one entry per t-segment, cell = l*mz + k.  */
+int orc_semicircle_arcs(const orc_geom* g, int h, int m, int32_t* cell, double* len, int cap) {
+  if (check_geom(g)) return -1;
+  const double hz = half_z(g), dl = dell(g);
+  const double ell = ell_centre(g, m), zc = ring_z(g, h);
+  int nt = 2 * (g->mz + 1) + 2 * (g->n_ell + 1) + 4;
+  double* tb = (double*)malloc(sizeof(double) * nt);
+  if (!tb) return -2;
+  int n = 0;
+  tb[n++] = 0.0;
+  tb[n++] = ORC_PI;
+  for (int k = 0; k <= g->mz; ++k) {
+    double u = -hz + k * g->dz - zc;
+    if (fabs(u) < ell) tb[n++] = atan2(sqrt((ell - u) * (ell + u)), u);
+  }
+  for (int l = 0; l <= g->n_ell; ++l) {
+    double rb = g->ell_lo + l * dl;
+    if (rb > 0.0 && rb < ell) {
+      double a = atan2(rb, sqrt((ell - rb) * (ell + rb)));
+      tb[n++] = a;
+      tb[n++] = ORC_PI - a;
+    }
+  }
+  qsort(tb, n, sizeof(double), cmp_double);
+  int out = 0;
+  for (int s = 0; s + 1 < n; ++s) {
+    double t0 = tb[s], t1 = tb[s + 1];
+    if (!(t1 > t0)) continue;
+    double tm = 0.5 * (t0 + t1);
+    int k = (int)floor((zc + ell * cos(tm) + hz) / g->dz);
+    int l = (int)floor((ell * sin(tm) - g->ell_lo) / dl);
+    if (k < 0 || k >= g->mz || l < 0 || l >= g->n_ell) continue;
+    if (out >= cap) {
+      free(tb);
+      return -3;
+    }
+    cell[out] = l * g->mz + k;
+    len[out] = ell * (t1 - t0);
+    ++out;
+  }
+  free(tb);
+  return out;
+}
+
+/* --------------------------------------------- per-voxel weight path
+ * Arc length of the circle (cx, cy, r) inside the box [x0,x1] x [y0,y1]:
+ * breakpoints where the circle meets the four box lines, midpoint test.    */
+static double arc_in_box(double cx, double cy, double r, double x0, double x1, double y0,
+                         double y1) {
+  double ab[8];
+  int n = 0;
+  double xs[2] = {x0, x1}, ys[2] = {y0, y1};
+  for (int i = 0; i < 2; ++i) {
+    double u = xs[i] - cx;
+    if (fabs(u) < r) {
+      double v = sqrt((r - u) * (r + u));
+      ab[n++] = wrap_2pi(atan2(v, u));
+      ab[n++] = wrap_2pi(atan2(-v, u));
+    }
+    u = ys[i] - cy;
+    if (fabs(u) < r) {
+      double v = sqrt((r - u) * (r + u));
+      ab[n++] = wrap_2pi(atan2(u, v));
+      ab[n++] = wrap_2pi(atan2(u, -v));
+    }
+  }
+  qsort(ab, n, sizeof(double), cmp_double);
+  double acc = 0.0;
+  int nseg = n > 0 ? n : 1;
+  for (int s = 0; s < nseg; ++s) {
+    double a0, a1;
+    if (n == 0) {
+      a0 = 0.0;
+      a1 = 2.0 * ORC_PI;
+    } else {
+      a0 = ab[s];
+      a1 = (s + 1 < n) ? ab[s + 1] : ab[0] + 2.0 * ORC_PI;
+    }
+    if (!(a1 > a0)) continue;
+    double am = 0.5 * (a0 + a1);
+    double x = cx + r * cos(am), y = cy + r * sin(am);
+    if (x > x0 && x < x1 && y > y0 && y < y1) acc += r * (a1 - a0);
+  }
+  return acc;
+}
+
+double orc_arc_in_box(double cx, double cy, double r, double x0, double x1, double y0, double y1) {
+  return arc_in_box(cx, cy, r, x0, x1, y0, y1);
+}
+
+/* Weight of voxel (ix, iy, k) in shell (j, h, m):
+ *   sum over radius bins l of  [arc of the (z,rho) semicircle in cell (k,l)]
+ *                            x [arc of the in-plane circle rho_l in pixel].  */
+static double point_weight(const orc_geom* g, int j, int h, int m, int ix, int iy, int k) {
+  const double hx = half_x(g), hz = half_z(g), dl = dell(g);
+  const double sx = sensor_x(g, j), sy = sensor_y(g, j);
+  const double ell = ell_centre(g, m), zc = ring_z(g, h);
+  const double px0 = -hx + ix * g->dxy, py0 = -hx + iy * g->dxy;
+  const double z0 = -hz + k * g->dz;
+  /* in-plane distance range from the sensor to the pixel: only bins whose
+   * centre radius lies in it (plus one bin of margin) can meet the pixel */
+  double cx = fmax(px0 - sx, fmax(0.0, sx - (px0 + g->dxy)));
+  double cy = fmax(py0 - sy, fmax(0.0, sy - (py0 + g->dxy)));
+  double fx = fmax(fabs(px0 - sx), fabs(px0 + g->dxy - sx));
+  double fy = fmax(fabs(py0 - sy), fabs(py0 + g->dxy - sy));
+  int l0 = (int)floor((sqrt(cx * cx + cy * cy) - g->ell_lo) / dl) - 1;
+  int l1 = (int)floor((sqrt(fx * fx + fy * fy) - g->ell_lo) / dl) + 1;
+  if (l0 < 0) l0 = 0;
+  if (l1 > g->n_ell - 1) l1 = g->n_ell - 1;
+  double acc = 0.0;
+  for (int l = l0; l <= l1; ++l) {
+    double rho = ell_centre(g, l);
+    double a1 = arc_in_box(sx, sy, rho, px0, px0 + g->dxy, py0, py0 + g->dxy);
+    if (a1 == 0.0) continue;
+    double rb0 = g->ell_lo + l * dl;
+    double a2 = arc_in_box(zc, 0.0, ell, z0, z0 + g->dz, rb0, rb0 + dl);
+    acc += a1 * a2;
+  }
+  return acc;
+}
+
+double orc_point_weight(const orc_geom* g, int j, int h, int m, int ix, int iy, int k) {
+  if (check_geom(g)) return -1.0;
+  return point_weight(g, j, h, m, ix, iy, k);
+}
+
+/* Adjoint at a list of voxels: voxels[3*i..] = (ix, iy, k).
+ * out[i] = sum over all shells of point_weight * p[shell].  Only shells whose
+ * radius range can reach the voxel box are visited.                        */
+int orc_adjoint_voxels(const orc_geom* g, const double* p, const int32_t* voxels, long n,
+                       double* out, int nthreads) {
+  if (check_geom(g)) return -1;
+  set_threads(nthreads);
+  const double hx = half_x(g), hz = half_z(g), dl = dell(g);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long i = 0; i < n; ++i) {
+    int ix = voxels[3 * i], iy = voxels[3 * i + 1], k = voxels[3 * i + 2];
+    double bx0 = -hx + ix * g->dxy, by0 = -hx + iy * g->dxy, bz0 = -hz + k * g->dz;
+    double acc = 0.0;
+    for (int j = 0; j < g->n_phi; ++j) {
+      double sx = sensor_x(g, j), sy = sensor_y(g, j);
+      for (int h = 0; h < g->n_zs; ++h) {
+        double zc = ring_z(g, h);
+        /* distance range from the sensor point to the voxel box */
+        double cx = fmax(bx0 - sx, fmax(0.0, sx - (bx0 + g->dxy)));
+        double cy = fmax(by0 - sy, fmax(0.0, sy - (by0 + g->dxy)));
+        double cz = fmax(bz0 - zc, fmax(0.0, zc - (bz0 + g->dz)));
+        double dmin = sqrt(cx * cx + cy * cy + cz * cz);
+        double fx = fmax(fabs(bx0 - sx), fabs(bx0 + g->dxy - sx));
+        double fy = fmax(fabs(by0 - sy), fabs(by0 + g->dxy - sy));
+        double fz = fmax(fabs(bz0 - zc), fabs(bz0 + g->dz - zc));
+        double dmax = sqrt(fx * fx + fy * fy + fz * fz);
+        int m0 = (int)floor((dmin - g->ell_lo) / dl) - 1;
+        int m1 = (int)floor((dmax - g->ell_lo) / dl) + 1;
+        if (m0 < 0) m0 = 0;
+        if (m1 > g->n_ell - 1) m1 = g->n_ell - 1;
+        for (int m = m0; m <= m1; ++m) {
+          double gv = p[((long)j * g->n_zs + h) * g->n_ell + m];
+          if (gv == 0.0) continue;
+          acc += gv * point_weight(g, j, h, m, ix, iy, k);
+        }
+      }
+    }
+    out[i] = acc;
+  }
+  return 0;
+}

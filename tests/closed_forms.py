@@ -1,0 +1,79 @@
+"""Closed forms used to pin the oracle (test helpers, independent of it).
+
+The arc of a circle inside an axis-parallel rectangle is computed here by the
+quadrant-interval method: in each quarter of the circle both cos and sin are
+monotone, so the angles whose x (resp. y) coordinate lies in the rectangle
+form one interval per quarter, given by acos/asin of the edge offsets.  The
+oracle instead sorts grid-line crossings and tests segment midpoints.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PI = math.pi
+
+
+def _acos_r(u: float, r: float) -> float:
+    """Angle in [0, pi] whose cosine is u/r (clamped)."""
+    if u >= r:
+        return 0.0
+    if u <= -r:
+        return PI
+    return math.atan2(math.sqrt((r - u) * (r + u)), u)
+
+
+def _asin_r(u: float, r: float) -> float:
+    """Angle in [-pi/2, pi/2] whose sine is u/r (clamped)."""
+    if u >= r:
+        return 0.5 * PI
+    if u <= -r:
+        return -0.5 * PI
+    return math.atan2(u, math.sqrt((r - u) * (r + u)))
+
+
+def _ov(*iv):
+    lo = max(a for a, _ in iv)
+    hi = min(b for _, b in iv)
+    return max(0.0, hi - lo)
+
+
+def arc_circle_rect(cx, cy, r, x0, x1, y0, y1) -> float:
+    """Length of the circle (cx, cy, r) inside [x0, x1] x [y0, y1]."""
+    a1, a0 = _acos_r(x1 - cx, r), _acos_r(x0 - cx, r)
+    s0, s1 = _asin_r(y0 - cy, r), _asin_r(y1 - cy, r)
+    t = 0.0
+    t += _ov((0.0, 0.5 * PI), (a1, a0), (s0, s1))                    # first quarter
+    t += _ov((0.5 * PI, PI), (a1, a0), (PI - s1, PI - s0))            # second
+    t += _ov((-PI, -0.5 * PI), (-a0, -a1), (-PI - s1, -PI - s0))      # third
+    t += _ov((-0.5 * PI, 0.0), (-a0, -a1), (s0, s1))                  # fourth
+    return r * t
+
+
+def ball_srt(sensor, centre, a, amp, ell) -> np.ndarray:
+    """Closed-form SRT of a uniform ball: area of the spherical cap of the shell
+    |x - sensor| = ell inside the ball, times amp.  Cap area 2*pi*ell*h with
+    h = ell - (d^2 + ell^2 - a^2) / (2 d) = (a^2 - (d - ell)^2) / (2 d)."""
+    d = float(np.linalg.norm(np.asarray(sensor) - np.asarray(centre)))
+    ell = np.asarray(ell, dtype=np.float64)
+    val = amp * PI * ell * (a * a - (d - ell) ** 2) / d
+    return np.where(np.abs(d - ell) <= a, val, 0.0)
+
+
+def geometry_numbers(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, phi0=0.0):
+    """Grid positions under the stated readings (cell-centred radii and rings,
+    centred voxel box)."""
+    H, L = mz * dz, ms * dxy
+    rxy = L / math.sqrt(2.0)
+    lo, hi = radius - rxy, radius + rxy
+    dl = (hi - lo) / n_ell
+    return dict(
+        L=L, H=H, lo=lo, hi=hi, dl=dl,
+        ell=lo + (np.arange(n_ell) + 0.5) * dl,
+        edges=lo + np.arange(n_ell + 1) * dl,
+        zh=-0.5 * H + (np.arange(n_zs) + 0.5) * H / n_zs,
+        zb=-0.5 * H + np.arange(mz + 1) * dz,
+        xb=-0.5 * L + np.arange(ms + 1) * dxy,
+        phi=phi0 + 2 * PI * np.arange(n_phi) / n_phi,
+    )
