@@ -1,0 +1,204 @@
+/*
+ * srt.h -- C ABI of the GB300 (sm_103a) discrete spherical Radon transform
+ * for a cylindrical sensor aperture.
+ *
+ * The transform follows the paper "An Efficient Implementation of the
+ * Spherical Radon Transform with Cylindrical Apertures" (Lozenski, Cam,
+ * Anastasio, Villa):
+ *   - Sec. 2: the SRT over a shell centred on the cylinder factors into an
+ *     in-plane circular Radon transform (CRT^{1,2}, radius l sin t, measure
+ *     (l sin t) da) followed by a CRT^{3,4} in the (z, rho) half plane
+ *     (semicircle centred (r3, 0), radius l, measure l dt);
+ *   - Sec. 3.1: piecewise-constant voxels, both CRTs as sparse matrices with
+ *     exact arc-length entries on a radius grid {l_l} shared by rho and l;
+ *     Algorithm 1 (forward) = A1 F, reshape, A2 Y, reshape;
+ *   - Sec. 3.2: Algorithm 2 (adjoint) = A2^T, reshape, A1^T: the matched
+ *     adjoint, the exact transpose of the forward.
+ *
+ * All compute runs in hand-written CUDA kernels on the device that was current
+ * when the plan was made.  There is no CPU fallback.  Every call returns an
+ * srt_status; nothing throws across the ABI.  Calls that take a stream are
+ * asynchronous on it (0 = legacy default stream).
+ */
+#ifndef SRT_H
+#define SRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum srt_status {
+  SRT_OK = 0,
+  SRT_ERR_ARG = 1,       /* null pointer, non-positive size, bad enum        */
+  SRT_ERR_GEOMETRY = 2,  /* invalid geometry or operator too large (int32)   */
+  SRT_ERR_OOM = 3,       /* device allocation failed during srt_plan          */
+  SRT_ERR_CUDA = 4,      /* a CUDA runtime call or launch failed              */
+  SRT_ERR_WORKSPACE = 5, /* workspace missing, too small or misaligned        */
+  SRT_ERR_TIMEOUT = 6,   /* host-side wait exceeded its deadline              */
+  SRT_ERR_NOT_READY = 7  /* timing data requested before any timed call       */
+};
+
+/* Storage type of the matrix entries; accumulation is always FP32. */
+enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
+
+/* Plan flags. */
+#define SRT_KEEP_F64 0x1 /* keep FP64 copies of A1/A2 entries for srt_plan_export */
+
+/*
+ * Geometry (Sec. 3.1, Algorithm 1 inputs).  Lengths in mm, angles in rad.
+ *   Volume: ms x ms x mz voxels of size dxy x dxy x dz, voxel centres at
+ *     ((i - (ms-1)/2) dxy, (j - (ms-1)/2) dxy, (k - (mz-1)/2) dz).
+ *   Sensor columns: (radius cos phi_j, radius sin phi_j), phi_j = phi0 +
+ *     2 pi j / n_phi, j < n_phi.  Requires radius > ms*dxy/sqrt(2).
+ *   Sensor rings: z_h = zs_lo + (h + 1/2)(zs_hi - zs_lo)/n_zs, h < n_zs.
+ *   Radius grid shared by the in-plane radius rho and the shell radius l:
+ *     bins [ell_lo + i d, ell_lo + (i+1) d], d = (ell_hi - ell_lo)/n_ell,
+ *     centres l_i = ell_lo + (i + 1/2) d; requires 0 < ell_lo < ell_hi.
+ *   weight_dtype: SRT_FP32 or SRT_BF16 (entries rounded once from FP64,
+ *     round-to-nearest-even; the adjoint uses the identical rounded values).
+ */
+typedef struct srt_geometry {
+  int32_t ms, mz;
+  double dxy, dz;
+  double radius;
+  int32_t n_phi;
+  double phi0;
+  int32_t n_zs;
+  double zs_lo, zs_hi;
+  int32_t n_ell;
+  double ell_lo, ell_hi;
+  int32_t weight_dtype;
+  int32_t flags;
+} srt_geometry;
+
+typedef struct srt_plan_s* srt_plan_t;
+
+/* Sizes of an assembled plan. */
+typedef struct srt_plan_info_t {
+  int64_t rows1, cols1, nnz1; /* A1 = A^{1,2}: (n_phi n_ell) x ms^2            */
+  int64_t rows2, cols2, nnz2; /* A2 = A^{3,4}: (n_zs n_ell) x (n_ell mz)       */
+  int64_t dropped1, dropped2; /* entries with 0 < length <= 1e-12 spacing     */
+  int64_t device_bytes;       /* device memory owned by the plan              */
+  int32_t weight_dtype;
+  int32_t reserved;
+} srt_plan_info_t;
+
+/*
+ * Fill *g with the default readings: rings at the cell centres of the volume
+ * height [-mz dz/2, mz dz/2], radius grid [R - r, R + r] with r = ms dxy /
+ * sqrt(2) (the in-plane half diagonal), phi0 = 0, FP32 weights, no flags.
+ * Returns SRT_ERR_ARG for a null g.
+ */
+int srt_geometry_default(srt_geometry* g, int32_t ms, int32_t mz, double dxy, double dz,
+                         double radius, int32_t n_phi, int32_t n_zs, int32_t n_ell);
+
+/*
+ * Build a plan on the current device (Sec. 3.1): assemble A1 and A2 from
+ * exact FP64 arc lengths, then the transposes A1^T, A2^T used by the adjoint
+ * (Sec. 3.2), all by device kernels on `stream`.  Synchronises the stream
+ * before returning.  The plan owns its device memory and is immutable: it may
+ * be used concurrently from several streams with distinct workspaces.
+ * Errors: SRT_ERR_ARG (null), SRT_ERR_GEOMETRY (invalid geometry, nnz >=
+ * 2^31), SRT_ERR_OOM, SRT_ERR_CUDA.  On error *out is set to NULL.
+ */
+int srt_plan(const srt_geometry* g, void* stream, srt_plan_t* out);
+
+/* Sizes of a plan.  Errors: SRT_ERR_ARG. */
+int srt_plan_info(srt_plan_t plan, srt_plan_info_t* out);
+
+/*
+ * Device workspace, in bytes, that srt_forward / srt_adjoint need for `batch`
+ * volumes (intermediates of Algorithm 1/2).  Errors: SRT_ERR_ARG.
+ */
+int srt_workspace_bytes(srt_plan_t plan, int32_t batch, size_t* bytes);
+
+/*
+ * Forward transform, Algorithm 1 on every sensor column at once:
+ *   f: device, float[batch][ms][ms][mz]        (read only, z fastest)
+ *   p: device, float[batch][n_phi][n_zs][n_ell] (overwritten, never accumulated)
+ *   workspace: device, >= srt_workspace_bytes(batch), 256-byte aligned; the
+ *   caller owns it; concurrent calls need distinct workspaces.
+ * f, p must be 16-byte aligned.  Asynchronous on `stream`.
+ * Errors: SRT_ERR_ARG, SRT_ERR_WORKSPACE, SRT_ERR_CUDA (launch failure).
+ */
+int srt_forward(srt_plan_t plan, const float* f, float* p, int32_t batch, void* workspace,
+                size_t workspace_bytes, void* stream);
+
+/*
+ * Matched adjoint, Algorithm 2 (A2^T then A1^T, gather form, no atomics):
+ *   p: device, float[batch][n_phi][n_zs][n_ell] (read only)
+ *   f: device, float[batch][ms][ms][mz]         (overwritten)
+ * Same workspace, alignment and error rules as srt_forward.
+ */
+int srt_adjoint(srt_plan_t plan, const float* p, float* f, int32_t batch, void* workspace,
+                size_t workspace_bytes, void* stream);
+
+/*
+ * End-to-end variants on HOST buffers (same layouts as above; pinned memory
+ * gives full copy speed).  The call copies the input to the device, runs the
+ * transform in `workspace`, copies the result back and synchronises the
+ * stream.  `workspace` must hold srt_host_workspace_bytes(batch) bytes of
+ * device memory (device copies of input and output plus the transform
+ * workspace).  Errors: as srt_forward.
+ */
+int srt_host_workspace_bytes(srt_plan_t plan, int32_t batch, size_t* bytes);
+int srt_forward_host(srt_plan_t plan, const float* f_host, float* p_host, int32_t batch,
+                     void* workspace, size_t workspace_bytes, void* stream);
+int srt_adjoint_host(srt_plan_t plan, const float* p_host, float* f_host, int32_t batch,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * FP64 inner product on the device: *out = sum_i (double)a[i] * (double)b[i],
+ * summed in a fixed order (deterministic).  a, b: device float[n]; out:
+ * device double[1]; workspace: device, >= srt_dot_workspace_bytes() bytes.
+ * Used for adjoint-identity checks <A f, g> = <f, A^T g>.
+ * Errors: SRT_ERR_ARG, SRT_ERR_WORKSPACE, SRT_ERR_CUDA.
+ */
+size_t srt_dot_workspace_bytes(void);
+int srt_dot_f64(const float* a, const float* b, int64_t n, double* out, void* workspace,
+                size_t workspace_bytes, void* stream);
+
+/*
+ * Copy an assembled operator to HOST memory, for inspection and tests.
+ *   which: 1 = A1, 2 = A2, 3 = A1^T, 4 = A2^T.
+ *   rowptr: int32[rows+1]; col: int32[nnz]; val32: float[nnz] (the stored
+ *   entries widened to FP32; may be NULL); val64: double[nnz] (the FP64
+ *   entries before rounding; requires SRT_KEEP_F64; may be NULL).
+ *   Rows are sorted by column index.  Synchronous.
+ * Errors: SRT_ERR_ARG (bad which, null rowptr/col, val64 without the flag),
+ * SRT_ERR_CUDA.
+ */
+int srt_plan_export(srt_plan_t plan, int32_t which, int32_t* rowptr, int32_t* col, float* val32,
+                    double* val64);
+
+/*
+ * Per-stage timing with CUDA events recorded on the launch stream.
+ * srt_plan_set_timing(plan, 1) makes every later srt_forward / srt_adjoint
+ * record events around each kernel stage; srt_stage_times(plan, dir, ms, n)
+ * then returns, for the LAST call in direction dir (0 forward, 1 adjoint), the
+ * elapsed milliseconds of its stages in launch order (n >= 4: first SpMM,
+ * permute, second SpMM, permute) after synchronising on the last event.
+ * Not for use with stream capture.  Errors: SRT_ERR_ARG, SRT_ERR_NOT_READY.
+ */
+int srt_plan_set_timing(srt_plan_t plan, int32_t enable);
+int srt_stage_times(srt_plan_t plan, int32_t dir, float* ms, int32_t n);
+
+/* Number of kernel launches one srt_forward / srt_adjoint call makes. */
+int srt_launches_per_call(srt_plan_t plan, int32_t dir, int32_t batch);
+
+/* Release the plan's device memory.  NULL is accepted.  Not stream-ordered:
+ * the caller must ensure no work using the plan is still in flight. */
+int srt_plan_destroy(srt_plan_t plan);
+
+/* Static description of a status code. */
+const char* srt_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRT_H */

@@ -1,0 +1,329 @@
+// C ABI of libsrt (declared in include/srt.h): plan management, the forward
+// transform (Algorithm 1 of the paper) and the matched adjoint (Algorithm 2).
+//
+// Forward, batch B, on every sensor column at once:
+//   SpMM1  Y1[b][(j,l)][k]  = A1 F_b                 (A1: Sec. 3.1, Alg. 1)
+//   P1     Y1'[(l,k)][b][j] <- Y1[b][j][(l,k)]       (Alg. 1 reshape)
+//   SpMM2  P'[(h,m)][b][j]  = A2 Y1'                 (one A2 for all columns,
+//                                                      so (b, j) are the dense
+//                                                      columns of one product)
+//   P2     p[b][j][(h,m)]   <- P'[(h,m)][b][j]       (Alg. 1 final reshape)
+// Adjoint (Alg. 2): P2^-1, A2^T, P1^-1, A1^T with the transposed matrices.
+#include <math.h>
+#include <new>
+
+#include "common.cuh"
+
+namespace {
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int64_t align256(int64_t b) { return (b + 255) & ~(int64_t)255; }
+
+// Elements of one intermediate buffer: max(|Y1|, |P'|) over the batch.
+int64_t buf_elems(const srt_geometry& g, int batch) {
+  const int64_t y1 = (int64_t)batch * g.n_phi * g.n_ell * g.mz;
+  const int64_t pp = (int64_t)batch * g.n_phi * g.n_zs * g.n_ell;
+  return y1 > pp ? y1 : pp;
+}
+
+int check_geometry(const srt_geometry& g) {
+  if (g.ms <= 0 || g.mz <= 0 || g.n_phi <= 0 || g.n_zs <= 0 || g.n_ell <= 0) return SRT_ERR_GEOMETRY;
+  if (!(g.dxy > 0) || !(g.dz > 0) || !(g.radius > 0)) return SRT_ERR_GEOMETRY;
+  if (!(g.ell_lo > 0) || !(g.ell_hi > g.ell_lo) || !(g.zs_hi > g.zs_lo)) return SRT_ERR_GEOMETRY;
+  if (!isfinite(g.phi0) || !isfinite(g.ell_hi) || !isfinite(g.zs_lo) || !isfinite(g.zs_hi))
+    return SRT_ERR_GEOMETRY;
+  if (!(g.radius > g.ms * g.dxy / sqrt(2.0))) return SRT_ERR_GEOMETRY;  // sensors outside
+  if (g.weight_dtype != SRT_FP32 && g.weight_dtype != SRT_BF16) return SRT_ERR_GEOMETRY;
+  // index ranges used in int32 arithmetic by the kernels
+  const int64_t pix = (int64_t)g.ms * g.ms, cells = (int64_t)g.n_ell * g.mz;
+  const int64_t r1 = (int64_t)g.n_phi * g.n_ell, r2 = (int64_t)g.n_zs * g.n_ell;
+  const int64_t lim = ((int64_t)1 << 31) - 1;
+  if (pix > lim || cells > lim || r1 > lim || r2 > lim) return SRT_ERR_GEOMETRY;
+  return SRT_OK;
+}
+
+void free_plan(srt_plan_s* p) {
+  if (!p) return;
+  srt_csr_free(&p->a1);
+  srt_csr_free(&p->a2);
+  srt_csr_free(&p->a1t);
+  srt_csr_free(&p->a2t);
+  for (int d = 0; d < 2; ++d)
+    for (int i = 0; i < 5; ++i)
+      if (p->ev[d][i]) cudaEventDestroy(p->ev[d][i]);
+  delete p;
+}
+
+inline void mark(srt_plan_s* p, int dir, int i, cudaStream_t st) {
+  if (p->timing) cudaEventRecord(p->ev[dir][i], st);
+}
+
+int check_ws(srt_plan_s* p, int batch, const void* ws, size_t ws_bytes) {
+  if (!ws || ((uintptr_t)ws & 255)) return SRT_ERR_WORKSPACE;
+  if ((int64_t)ws_bytes < 2 * align256(buf_elems(p->g, batch) * 4)) return SRT_ERR_WORKSPACE;
+  return SRT_OK;
+}
+
+int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, float* w1,
+                cudaStream_t st) {
+  const srt_geometry& g = p->g;
+  const int64_t pix = (int64_t)g.ms * g.ms, r1 = (int64_t)g.n_phi * g.n_ell;
+  const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
+  const int64_t nb = (int64_t)B * g.n_phi;  // dense width of the second stage
+  mark(p, 0, 0, st);
+  SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B, st));
+  mark(p, 0, 1, st);
+  SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
+  mark(p, 0, 2, st);
+  SRT_TRY(srt_spmm(p->a2, g.weight_dtype, w1, nb, 0, w0, nb, 0, (int)nb, 1, st));
+  mark(p, 0, 3, st);
+  SRT_TRY(srt_transpose(w0, nb, g.n_phi, out, r2, (int64_t)g.n_phi * r2, (int)r2, g.n_phi, B, st));
+  mark(p, 0, 4, st);
+  if (p->timing) p->have_times[0] = 1;
+  return SRT_OK;
+}
+
+int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, float* w1,
+                cudaStream_t st) {
+  const srt_geometry& g = p->g;
+  const int64_t pix = (int64_t)g.ms * g.ms, r1 = (int64_t)g.n_phi * g.n_ell;
+  const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
+  const int64_t nb = (int64_t)B * g.n_phi;
+  mark(p, 1, 0, st);
+  SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
+  mark(p, 1, 1, st);
+  SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));
+  mark(p, 1, 2, st);
+  SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
+  mark(p, 1, 3, st);
+  SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, w0, g.mz, r1 * g.mz, f, g.mz, pix * g.mz, g.mz, B, st));
+  mark(p, 1, 4, st);
+  if (p->timing) p->have_times[1] = 1;
+  return SRT_OK;
+}
+
+int common_checks(srt_plan_t plan, const void* a, const void* b, int32_t batch) {
+  if (!plan || !a || !b || batch <= 0) return SRT_ERR_ARG;
+  if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return SRT_ERR_ARG;
+  return SRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int srt_geometry_default(srt_geometry* g, int32_t ms, int32_t mz, double dxy, double dz,
+                         double radius, int32_t n_phi, int32_t n_zs, int32_t n_ell) {
+  if (!g) return SRT_ERR_ARG;
+  const double h = mz * dz, rxy = ms * dxy / sqrt(2.0);
+  g->ms = ms;
+  g->mz = mz;
+  g->dxy = dxy;
+  g->dz = dz;
+  g->radius = radius;
+  g->n_phi = n_phi;
+  g->phi0 = 0.0;
+  g->n_zs = n_zs;
+  g->zs_lo = -0.5 * h;
+  g->zs_hi = 0.5 * h;
+  g->n_ell = n_ell;
+  g->ell_lo = radius - rxy;
+  g->ell_hi = radius + rxy;
+  g->weight_dtype = SRT_FP32;
+  g->flags = 0;
+  return SRT_OK;
+}
+
+int srt_plan(const srt_geometry* g, void* stream, srt_plan_t* out) {
+  if (!out) return SRT_ERR_ARG;
+  *out = nullptr;
+  if (!g) return SRT_ERR_ARG;
+  SRT_TRY(check_geometry(*g));
+  srt_plan_s* p = new (std::nothrow) srt_plan_s();
+  if (!p) return SRT_ERR_OOM;
+  p->g = *g;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return SRT_ERR_CUDA;
+  }
+  int s = srt_assemble(p, S(stream));
+  if (s != SRT_OK) {
+    cudaStreamSynchronize(S(stream));
+    cudaGetLastError();
+    free_plan(p);
+    return s;
+  }
+  *out = p;
+  return SRT_OK;
+}
+
+int srt_plan_info(srt_plan_t p, srt_plan_info_t* o) {
+  if (!p || !o) return SRT_ERR_ARG;
+  o->rows1 = p->a1.rows;
+  o->cols1 = p->a1.cols;
+  o->nnz1 = p->a1.nnz;
+  o->rows2 = p->a2.rows;
+  o->cols2 = p->a2.cols;
+  o->nnz2 = p->a2.nnz;
+  o->dropped1 = p->dropped1;
+  o->dropped2 = p->dropped2;
+  o->device_bytes = p->bytes;
+  o->weight_dtype = p->g.weight_dtype;
+  o->reserved = 0;
+  return SRT_OK;
+}
+
+int srt_workspace_bytes(srt_plan_t p, int32_t batch, size_t* bytes) {
+  if (!p || !bytes || batch <= 0) return SRT_ERR_ARG;
+  *bytes = (size_t)(2 * align256(buf_elems(p->g, batch) * 4));
+  return SRT_OK;
+}
+
+int srt_forward(srt_plan_t p, const float* f, float* out, int32_t batch, void* ws,
+                size_t ws_bytes, void* stream) {
+  SRT_TRY(common_checks(p, f, out, batch));
+  SRT_TRY(check_ws(p, batch, ws, ws_bytes));
+  float* w0 = (float*)ws;
+  float* w1 = w0 + align256(buf_elems(p->g, batch) * 4) / 4;
+  return run_forward(p, f, out, batch, w0, w1, S(stream));
+}
+
+int srt_adjoint(srt_plan_t p, const float* in, float* f, int32_t batch, void* ws,
+                size_t ws_bytes, void* stream) {
+  SRT_TRY(common_checks(p, in, f, batch));
+  SRT_TRY(check_ws(p, batch, ws, ws_bytes));
+  float* w0 = (float*)ws;
+  float* w1 = w0 + align256(buf_elems(p->g, batch) * 4) / 4;
+  return run_adjoint(p, in, f, batch, w0, w1, S(stream));
+}
+
+int srt_host_workspace_bytes(srt_plan_t p, int32_t batch, size_t* bytes) {
+  if (!p || !bytes || batch <= 0) return SRT_ERR_ARG;
+  const srt_geometry& g = p->g;
+  const int64_t nf = (int64_t)batch * g.ms * g.ms * g.mz;
+  const int64_t np = (int64_t)batch * g.n_phi * g.n_zs * g.n_ell;
+  *bytes = (size_t)(align256(nf * 4) + align256(np * 4) + 2 * align256(buf_elems(g, batch) * 4));
+  return SRT_OK;
+}
+
+static int host_call(srt_plan_t p, int dir, const float* in_h, float* out_h, int32_t batch,
+                     void* ws, size_t ws_bytes, void* stream) {
+  if (!p || !in_h || !out_h || batch <= 0) return SRT_ERR_ARG;
+  size_t need = 0;
+  srt_host_workspace_bytes(p, batch, &need);
+  if (!ws || ((uintptr_t)ws & 255) || ws_bytes < need) return SRT_ERR_WORKSPACE;
+  const srt_geometry& g = p->g;
+  const int64_t nf = (int64_t)batch * g.ms * g.ms * g.mz;
+  const int64_t np = (int64_t)batch * g.n_phi * g.n_zs * g.n_ell;
+  float* df = (float*)ws;
+  float* dp = df + align256(nf * 4) / 4;
+  float* w0 = dp + align256(np * 4) / 4;
+  float* w1 = w0 + align256(buf_elems(g, batch) * 4) / 4;
+  cudaStream_t st = S(stream);
+  if (dir == 0) {
+    SRT_CUDA_TRY(cudaMemcpyAsync(df, in_h, nf * 4, cudaMemcpyHostToDevice, st));
+    SRT_TRY(run_forward(p, df, dp, batch, w0, w1, st));
+    SRT_CUDA_TRY(cudaMemcpyAsync(out_h, dp, np * 4, cudaMemcpyDeviceToHost, st));
+  } else {
+    SRT_CUDA_TRY(cudaMemcpyAsync(dp, in_h, np * 4, cudaMemcpyHostToDevice, st));
+    SRT_TRY(run_adjoint(p, dp, df, batch, w0, w1, st));
+    SRT_CUDA_TRY(cudaMemcpyAsync(out_h, df, nf * 4, cudaMemcpyDeviceToHost, st));
+  }
+  SRT_CUDA_TRY(cudaStreamSynchronize(st));
+  return SRT_OK;
+}
+
+int srt_forward_host(srt_plan_t p, const float* f_host, float* p_host, int32_t batch, void* ws,
+                     size_t ws_bytes, void* stream) {
+  return host_call(p, 0, f_host, p_host, batch, ws, ws_bytes, stream);
+}
+
+int srt_adjoint_host(srt_plan_t p, const float* p_host, float* f_host, int32_t batch, void* ws,
+                     size_t ws_bytes, void* stream) {
+  return host_call(p, 1, p_host, f_host, batch, ws, ws_bytes, stream);
+}
+
+size_t srt_dot_workspace_bytes(void) { return (size_t)SRT_DOT_BLOCKS * sizeof(double); }
+
+int srt_dot_f64(const float* a, const float* b, int64_t n, double* out, void* ws, size_t ws_bytes,
+                void* stream) {
+  if (!a || !b || !out || n < 0) return SRT_ERR_ARG;
+  if (!ws || ((uintptr_t)ws & 7) || ws_bytes < srt_dot_workspace_bytes()) return SRT_ERR_WORKSPACE;
+  return srt_dot(a, b, n, out, (double*)ws, S(stream));
+}
+
+int srt_plan_export(srt_plan_t p, int32_t which, int32_t* rowptr, int32_t* col, float* val32,
+                    double* val64) {
+  if (!p || !rowptr || !col) return SRT_ERR_ARG;
+  const SrtCsr* m = which == 1 ? &p->a1 : which == 2 ? &p->a2 : which == 3 ? &p->a1t
+                  : which == 4 ? &p->a2t : nullptr;
+  if (!m) return SRT_ERR_ARG;
+  if (val64 && !m->v64) return SRT_ERR_ARG;
+  SRT_CUDA_TRY(cudaMemcpy(rowptr, m->rowptr, ((size_t)m->rows + 1) * 4, cudaMemcpyDeviceToHost));
+  SRT_CUDA_TRY(cudaMemcpy(col, m->col, (size_t)m->nnz * 4, cudaMemcpyDeviceToHost));
+  if (val64) SRT_CUDA_TRY(cudaMemcpy(val64, m->v64, (size_t)m->nnz * 8, cudaMemcpyDeviceToHost));
+  if (val32) {
+    if (m->v32) {
+      SRT_CUDA_TRY(cudaMemcpy(val32, m->v32, (size_t)m->nnz * 4, cudaMemcpyDeviceToHost));
+    } else {
+      uint16_t* tmp = new (std::nothrow) uint16_t[m->nnz > 0 ? m->nnz : 1];
+      if (!tmp) return SRT_ERR_OOM;
+      cudaError_t e = cudaMemcpy(tmp, m->v16, (size_t)m->nnz * 2, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess)
+        for (int64_t i = 0; i < m->nnz; ++i) {
+          const uint32_t u = ((uint32_t)tmp[i]) << 16;
+          memcpy(&val32[i], &u, 4);
+        }
+      delete[] tmp;
+      if (e != cudaSuccess) return SRT_ERR_CUDA;
+    }
+  }
+  return SRT_OK;
+}
+
+int srt_plan_set_timing(srt_plan_t p, int32_t enable) {
+  if (!p) return SRT_ERR_ARG;
+  if (enable && !p->ev[0][0]) {
+    for (int d = 0; d < 2; ++d)
+      for (int i = 0; i < 5; ++i) SRT_CUDA_TRY(cudaEventCreate(&p->ev[d][i]));
+  }
+  p->timing = enable ? 1 : 0;
+  p->have_times[0] = p->have_times[1] = 0;
+  return SRT_OK;
+}
+
+int srt_stage_times(srt_plan_t p, int32_t dir, float* ms, int32_t n) {
+  if (!p || !ms || dir < 0 || dir > 1 || n < 4) return SRT_ERR_ARG;
+  if (!p->have_times[dir]) return SRT_ERR_NOT_READY;
+  SRT_CUDA_TRY(cudaEventSynchronize(p->ev[dir][4]));
+  for (int i = 0; i < 4; ++i) SRT_CUDA_TRY(cudaEventElapsedTime(&ms[i], p->ev[dir][i], p->ev[dir][i + 1]));
+  return SRT_OK;
+}
+
+int srt_launches_per_call(srt_plan_t p, int32_t dir, int32_t batch) {
+  (void)dir;
+  (void)batch;
+  return p ? 4 : 0;
+}
+
+int srt_plan_destroy(srt_plan_t p) {
+  free_plan(p);
+  return SRT_OK;
+}
+
+const char* srt_error_string(int code) {
+  switch (code) {
+    case SRT_OK: return "success";
+    case SRT_ERR_ARG: return "invalid argument";
+    case SRT_ERR_GEOMETRY: return "invalid geometry or operator too large";
+    case SRT_ERR_OOM: return "out of device memory";
+    case SRT_ERR_CUDA: return "CUDA runtime error";
+    case SRT_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case SRT_ERR_TIMEOUT: return "wait timed out";
+    case SRT_ERR_NOT_READY: return "no timed call recorded";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,449 @@
+// Assembly of the two circular-Radon-transform matrices (Sec. 3.1 of the
+// paper) and of their transposes for the matched adjoint (Sec. 3.2).
+//
+// A1 = A^{1,2}: row r = j*n_ell + l is the circle of sensor column j
+//   (centre (R cos phi_j, R sin phi_j)) with bin-centre radius rho_l; column
+//   p = ix*ms + iy is a pixel; the entry is the exact arc length of the circle
+//   inside the pixel (in-plane CRT, measure rho da, Sec. 2).
+// A2 = A^{3,4}: row r = h*n_ell + m is the semicircle of ring h (centre
+//   (z_h, 0) in the (z, rho) half plane) with radius l_m; column c = l*mz + k
+//   is the cell slab k x radius bin l; the entry is the exact arc length of
+//   the semicircle inside the cell (vertical CRT, measure l dt, Sec. 2).
+//   Every cell has rho >= ell_lo > 0, so the full circle's lower half never
+//   meets a cell and the full-circle arc length equals the semicircle's.
+//
+// Lengths are computed in FP64 (srt_arc_in_rect), rounded once to the stored
+// type.  Rows are enumerated strip by strip (pixel columns for A1, radius bins
+// for A2): in each strip the circle's two branches cover a range of the other
+// index, widened by one cell each side, and every candidate's exact length is
+// computed; lengths <= 1e-12 x spacing are dropped (tangent touches).  The
+// count pass and the fill pass run the same enumeration, so they agree.
+#include <string.h>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct GeomDev {
+  int ms, mz, n_phi, n_zs, n_ell;
+  double dxy, dz, radius, phi0, zs_lo, zs_hi, ell_lo, ell_hi;
+  double hx, hz, dl, thr1, thr2;
+};
+
+GeomDev make_geom(const srt_geometry& g) {
+  GeomDev G;
+  G.ms = g.ms;
+  G.mz = g.mz;
+  G.n_phi = g.n_phi;
+  G.n_zs = g.n_zs;
+  G.n_ell = g.n_ell;
+  G.dxy = g.dxy;
+  G.dz = g.dz;
+  G.radius = g.radius;
+  G.phi0 = g.phi0;
+  G.zs_lo = g.zs_lo;
+  G.zs_hi = g.zs_hi;
+  G.ell_lo = g.ell_lo;
+  G.ell_hi = g.ell_hi;
+  G.hx = 0.5 * g.ms * g.dxy;
+  G.hz = 0.5 * g.mz * g.dz;
+  G.dl = (g.ell_hi - g.ell_lo) / g.n_ell;
+  G.thr1 = 1e-12 * g.dxy;
+  G.thr2 = 1e-12 * fmin(g.dz, G.dl);
+  return G;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Pixel/slab index range [lo, hi] covering the coordinate interval [a, b]
+// (origin at -half, spacing d), widened by one each side and clamped.
+__device__ __forceinline__ void cover(double a, double b, double half, double d, int n, int& lo,
+                                      int& hi) {
+  lo = clampi((int)floor((a + half) / d) - 1, 0, n - 1);
+  hi = clampi((int)floor((b + half) / d) + 1, 0, n - 1);
+}
+
+// Enumerate one strip.  The strip spans [s0, s1] along the strip axis; the
+// circle (centre (cu, cv) in (strip axis, cross axis), radius r) has two
+// branches over it.  For every candidate cross index q (ascending) the exact
+// length inside the cell is computed; f(q, w) is called for w > thr.
+// Returns the number of kept entries; *drop counts 0 < w <= thr.
+template <bool A1, class F>
+__device__ int strip_enum(const GeomDev& G, double cu, double cv, double r, int s, int& drop, F f) {
+  double s0, s1, half, d;
+  int n;
+  if (A1) {  // strip = pixel column ix, cross axis = y
+    s0 = -G.hx + s * G.dxy;
+    s1 = -G.hx + (s + 1) * G.dxy;
+    half = G.hx;
+    d = G.dxy;
+    n = G.ms;
+  } else {  // strip = radius bin l, cross axis = z
+    s0 = G.ell_lo + s * G.dl;
+    s1 = G.ell_lo + (s + 1) * G.dl;
+    half = G.hz;
+    d = G.dz;
+    n = G.mz;
+  }
+  const double u0 = s0 - cu, u1 = s1 - cu;
+  const double umin = (u0 <= 0.0 && u1 >= 0.0) ? 0.0 : fmin(fabs(u0), fabs(u1));
+  const double umax = fmax(fabs(u0), fabs(u1));
+  if (umin >= r) return 0;
+  const double thi = sqrt((r - umin) * (r + umin));
+  const double tlo = umax >= r ? 0.0 : sqrt((r - umax) * (r + umax));
+  int a0, a1, b0, b1;
+  cover(cv - thi, cv - tlo, half, d, n, a0, a1);
+  cover(cv + tlo, cv + thi, half, d, n, b0, b1);
+  if (b0 <= a1) b0 = a1 + 1;  // union, ascending
+  const double thr = A1 ? G.thr1 : G.thr2;
+  int kept = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const int q0 = pass ? b0 : a0, q1 = pass ? b1 : a1;
+    for (int q = q0; q <= q1; ++q) {
+      const double c0 = -half + q * d, c1 = -half + (q + 1) * d;
+      double w;
+      if (A1)
+        w = srt_arc_in_rect(cu, cv, r, s0, s1, c0, c1);
+      else  // (z, rho) plane: x = z, y = rho
+        w = srt_arc_in_rect(cv, cu, r, c0, c1, s0, s1);
+      if (w > thr) {
+        f(q, w, kept);
+        ++kept;
+      } else if (w > 0.0) {
+        ++drop;
+      }
+    }
+  }
+  return kept;
+}
+
+// One warp per row.  pass 0: counts[row] = entries, drops summed into *dropped.
+// pass 1: write (column, FP64 length) at rowptr[row] in ascending column order.
+template <bool A1>
+__global__ void __launch_bounds__(256) k_assemble(GeomDev G, int rows, int pass,
+                                                  int32_t* __restrict__ counts,
+                                                  const int32_t* __restrict__ rowptr,
+                                                  int32_t* __restrict__ col,
+                                                  double* __restrict__ val,
+                                                  unsigned long long* __restrict__ dropped) {
+  const int lane = threadIdx.x & 31;
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (row >= rows) return;  // warp-uniform
+  double cu, cv, r;
+  const int nstrips = A1 ? G.ms : G.n_ell;
+  if (A1) {
+    const int j = row / G.n_ell, l = row % G.n_ell;
+    const double phi = G.phi0 + 2.0 * SRT_PI * j / G.n_phi;
+    cu = G.radius * cos(phi);  // x of the sensor column (strip axis)
+    cv = G.radius * sin(phi);  // y
+    r = G.ell_lo + (l + 0.5) * G.dl;
+  } else {
+    const int h = row / G.n_ell, m = row % G.n_ell;
+    cu = 0.0;                                                   // rho of the centre
+    cv = G.zs_lo + (h + 0.5) * (G.zs_hi - G.zs_lo) / G.n_zs;    // z of the centre
+    r = G.ell_lo + (m + 0.5) * G.dl;
+  }
+  const int64_t base = pass ? rowptr[row] : 0;
+  const int64_t end = pass ? rowptr[row + 1] : 0;
+  const int stride = A1 ? G.ms : G.mz;
+  int total = 0, drop = 0, dummy = 0;
+  // One emitter for the count and the fill, so both run the same code.
+  bool write = false;
+  int64_t at = 0;
+  int strip = 0;
+  auto emit = [&](int q, double w, int i) {
+    if (write && at + i < end) {
+      col[at + i] = strip * stride + q;
+      val[at + i] = w;
+    }
+  };
+  for (int s0 = 0; s0 < nstrips; s0 += 32) {
+    strip = s0 + lane;
+    int cnt = 0;
+    write = false;
+    if (strip < nstrips) cnt = strip_enum<A1>(G, cu, cv, r, strip, pass ? dummy : drop, emit);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (pass && cnt > 0) {
+      at = base + total + (incl - cnt);
+      write = true;
+      strip_enum<A1>(G, cu, cv, r, strip, dummy, emit);
+    }
+    total += __shfl_sync(FULL, incl, 31);
+  }
+  if (!pass) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) drop += __shfl_xor_sync(FULL, drop, o);
+    if (lane == 0) {
+      counts[row] = total;
+      if (drop) atomicAdd(dropped, (unsigned long long)drop);
+    }
+  }
+}
+
+// Exclusive scan of n int32 counts into out[0..n] (out[n] = total) with a
+// 64-bit running sum; *total receives the exact 64-bit total.  One block.
+__global__ void __launch_bounds__(1024) k_scan(const int32_t* __restrict__ in,
+                                               int32_t* __restrict__ out, int64_t n,
+                                               long long* __restrict__ total) {
+  constexpr int ITEMS = 8;
+  __shared__ long long warp_sum[32];
+  __shared__ long long carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < n; base += 1024 * ITEMS) {
+    long long v[ITEMS];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int64_t idx = base + (int64_t)tid * ITEMS + i;
+      v[i] = idx < n ? in[idx] : 0;
+      s += v[i];
+    }
+    long long incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long t = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      long long w = warp_sum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(FULL, w, o);
+        if (lane >= o) w += t;
+      }
+      warp_sum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    long long run = carry + (wid ? warp_sum[wid - 1] : 0) + incl - s;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const int64_t idx = base + (int64_t)tid * ITEMS + i;
+      if (idx < n) out[idx] = (int32_t)run;
+      run += v[i];
+    }
+    __syncthreads();
+    if (tid == 0) carry += warp_sum[31];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out[n] = (int32_t)carry;
+    *total = carry;
+  }
+}
+
+__global__ void k_round(const double* __restrict__ v64, int64_t n, float* __restrict__ v32,
+                        uint16_t* __restrict__ v16) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = v64[i];
+    if (v32) v32[i] = __double2float_rn(w);
+    if (v16) v16[i] = srt_f64_to_bf16(w);
+  }
+}
+
+// ---- transpose: rows are grouped in blocks of rb consecutive rows ----------
+// cnt[b][c] = entries of block b in column c.
+__global__ void k_block_count(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                              int rb, int cols, int32_t* __restrict__ cnt) {
+  const int b = blockIdx.x;
+  const int64_t e0 = rowptr[(int64_t)b * rb], e1 = rowptr[(int64_t)(b + 1) * rb];
+  int32_t* c = cnt + (int64_t)b * cols;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(&c[col[e]], 1);
+}
+
+// Per column: exclusive prefix over blocks (in place) and the column total.
+__global__ void k_col_prefix(int32_t* __restrict__ cnt, int nblocks, int cols,
+                             int32_t* __restrict__ tot) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  int32_t run = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    const int64_t i = (int64_t)b * cols + c;
+    const int32_t v = cnt[i];
+    cnt[i] = run;
+    run += v;
+  }
+  tot[c] = run;
+}
+
+// Scatter block b's rows in row order: each row's columns are distinct, so a
+// row's entries are written concurrently; rows follow each other after a
+// barrier.  Output rows come out sorted by source row, values copied bitwise.
+__global__ void k_block_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const float* __restrict__ v32, const uint16_t* __restrict__ v16,
+                             const double* __restrict__ v64, int rb, int cols,
+                             const int32_t* __restrict__ tptr, int32_t* __restrict__ cur,
+                             int32_t* __restrict__ tcol, float* __restrict__ t32,
+                             uint16_t* __restrict__ t16, double* __restrict__ t64) {
+  const int b = blockIdx.x;
+  int32_t* c = cur + (int64_t)b * cols;
+  for (int r = b * rb; r < (b + 1) * rb; ++r) {
+    const int32_t e0 = rowptr[r], e1 = rowptr[r + 1];
+    for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int32_t k = col[e];
+      const int64_t pos = (int64_t)tptr[k] + c[k];
+      c[k] += 1;
+      tcol[pos] = r;
+      if (t32) t32[pos] = v32[e];
+      if (t16) t16[pos] = v16[e];
+      if (t64) t64[pos] = v64[e];
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+int dmalloc(T** p, int64_t n, int64_t* bytes) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, (size_t)n * sizeof(T));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return SRT_ERR_OOM;
+  }
+  if (e != cudaSuccess) return SRT_ERR_CUDA;
+  if (bytes) *bytes += n * (int64_t)sizeof(T);
+  return SRT_OK;
+}
+
+struct Tmp {  // device temporaries freed on every exit path
+  void* p[8] = {};
+  int n = 0;
+  ~Tmp() {
+    for (int i = 0; i < n; ++i) cudaFree(p[i]);
+  }
+  template <class T>
+  int get(T** out, int64_t count) {
+    int s = dmalloc(out, count, nullptr);
+    if (s == SRT_OK) p[n++] = *out;
+    return s;
+  }
+};
+
+int scan_counts(const int32_t* counts, int32_t* out, int64_t n, long long* dtotal, int64_t* total,
+                cudaStream_t st) {
+  k_scan<<<1, 1024, 0, st>>>(counts, out, n, dtotal);
+  SRT_CUDA_TRY(cudaGetLastError());
+  long long t = 0;
+  SRT_CUDA_TRY(cudaMemcpyAsync(&t, dtotal, sizeof(t), cudaMemcpyDeviceToHost, st));
+  SRT_CUDA_TRY(cudaStreamSynchronize(st));
+  *total = t;
+  return SRT_OK;
+}
+
+// Assemble one operator (A1 if a1, else A2) into m, FP64 lengths rounded to
+// the plan's type; the FP64 lengths stay in m->v64 for the caller to keep or free.
+template <bool A1>
+int assemble_one(const GeomDev& G, int wdt, SrtCsr* m, int64_t* dropped,
+                 int64_t* bytes, cudaStream_t st) {
+  const int rows = A1 ? G.n_phi * G.n_ell : G.n_zs * G.n_ell;
+  const int cols = A1 ? G.ms * G.ms : G.n_ell * G.mz;
+  m->rows = rows;
+  m->cols = cols;
+  Tmp tmp;
+  int32_t* counts;
+  long long* dtot;
+  unsigned long long* ddrop;
+  SRT_TRY(tmp.get(&counts, rows));
+  SRT_TRY(tmp.get(&dtot, 1));
+  SRT_TRY(tmp.get(&ddrop, 1));
+  SRT_CUDA_TRY(cudaMemsetAsync(ddrop, 0, sizeof(unsigned long long), st));
+  SRT_TRY(dmalloc(&m->rowptr, (int64_t)rows + 1, bytes));
+  const int threads = 256;
+  const int blocks = (int)(((int64_t)rows * 32 + threads - 1) / threads);
+  k_assemble<A1><<<blocks, threads, 0, st>>>(G, rows, 0, counts, nullptr, nullptr, nullptr, ddrop);
+  SRT_CUDA_TRY(cudaGetLastError());
+  int64_t nnz = 0;
+  SRT_TRY(scan_counts(counts, m->rowptr, rows, dtot, &nnz, st));
+  if (nnz >= ((int64_t)1 << 31)) return SRT_ERR_GEOMETRY;
+  m->nnz = nnz;
+  unsigned long long dr = 0;
+  SRT_CUDA_TRY(cudaMemcpyAsync(&dr, ddrop, sizeof(dr), cudaMemcpyDeviceToHost, st));
+  double* v64;
+  SRT_TRY(dmalloc(&m->col, nnz, bytes));
+  SRT_TRY(dmalloc(&v64, nnz, nullptr));
+  m->v64 = v64;  // owned by m until released below
+  k_assemble<A1><<<blocks, threads, 0, st>>>(G, rows, 1, nullptr, m->rowptr, m->col, v64, nullptr);
+  SRT_CUDA_TRY(cudaGetLastError());
+  if (wdt == SRT_BF16)
+    SRT_TRY(dmalloc(&m->v16, nnz, bytes));
+  else
+    SRT_TRY(dmalloc(&m->v32, nnz, bytes));
+  k_round<<<1216, 256, 0, st>>>(v64, nnz, m->v32, m->v16);
+  SRT_CUDA_TRY(cudaGetLastError());
+  SRT_CUDA_TRY(cudaStreamSynchronize(st));
+  *dropped = (int64_t)dr;
+  return SRT_OK;
+}
+
+// t = transpose of a (rows grouped in blocks of rb for deterministic order).
+int transpose_csr(const SrtCsr& a, int rb, SrtCsr* t, int64_t* bytes, cudaStream_t st) {
+  t->rows = a.cols;
+  t->cols = a.rows;
+  t->nnz = a.nnz;
+  const int nb = a.rows / rb;
+  Tmp tmp;
+  int32_t *cnt, *tot;
+  long long* dtot;
+  SRT_TRY(tmp.get(&cnt, (int64_t)nb * a.cols));
+  SRT_TRY(tmp.get(&tot, a.cols));
+  SRT_TRY(tmp.get(&dtot, 1));
+  SRT_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)nb * a.cols * sizeof(int32_t), st));
+  k_block_count<<<nb, 512, 0, st>>>(a.rowptr, a.col, rb, a.cols, cnt);
+  SRT_CUDA_TRY(cudaGetLastError());
+  k_col_prefix<<<(a.cols + 255) / 256, 256, 0, st>>>(cnt, nb, a.cols, tot);
+  SRT_CUDA_TRY(cudaGetLastError());
+  SRT_TRY(dmalloc(&t->rowptr, (int64_t)a.cols + 1, bytes));
+  int64_t nnz = 0;
+  SRT_TRY(scan_counts(tot, t->rowptr, a.cols, dtot, &nnz, st));
+  if (nnz != a.nnz) return SRT_ERR_CUDA;
+  SRT_TRY(dmalloc(&t->col, nnz, bytes));
+  if (a.v32) SRT_TRY(dmalloc(&t->v32, nnz, bytes));
+  if (a.v16) SRT_TRY(dmalloc(&t->v16, nnz, bytes));
+  if (a.v64) SRT_TRY(dmalloc(&t->v64, nnz, bytes));
+  k_block_fill<<<nb, 512, 0, st>>>(a.rowptr, a.col, a.v32, a.v16, a.v64, rb, a.cols, t->rowptr,
+                                   cnt, t->col, t->v32, t->v16, t->v64);
+  SRT_CUDA_TRY(cudaGetLastError());
+  SRT_CUDA_TRY(cudaStreamSynchronize(st));
+  return SRT_OK;
+}
+
+}  // namespace
+
+void srt_csr_free(SrtCsr* m) {
+  cudaFree(m->rowptr);
+  cudaFree(m->col);
+  cudaFree(m->v32);
+  cudaFree(m->v16);
+  cudaFree(m->v64);
+  *m = SrtCsr();
+}
+
+int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
+  const GeomDev G = make_geom(plan->g);
+  const bool keep = (plan->g.flags & SRT_KEEP_F64) != 0;
+  const int wdt = plan->g.weight_dtype;
+  SRT_TRY(assemble_one<true>(G, wdt, &plan->a1, &plan->dropped1, &plan->bytes, st));
+  SRT_TRY(assemble_one<false>(G, wdt, &plan->a2, &plan->dropped2, &plan->bytes, st));
+  if (!keep) {  // FP64 lengths are only needed for export: drop before transposing
+    cudaFree(plan->a1.v64);
+    cudaFree(plan->a2.v64);
+    plan->a1.v64 = plan->a2.v64 = nullptr;
+  } else {
+    plan->bytes += (plan->a1.nnz + plan->a2.nnz) * (int64_t)sizeof(double);
+  }
+  SRT_TRY(transpose_csr(plan->a1, G.n_ell, &plan->a1t, &plan->bytes, st));
+  SRT_TRY(transpose_csr(plan->a2, G.n_ell, &plan->a2t, &plan->bytes, st));
+  return SRT_OK;
+}

@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of libsrt.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "srt.h"
+
+#define SRT_PI 3.14159265358979323846264338327950288
+
+// Return SRT_ERR_CUDA from the enclosing function when a runtime call fails.
+#define SRT_CUDA_TRY(expr)                         \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return SRT_ERR_CUDA;    \
+  } while (0)
+
+#define SRT_TRY(expr)                 \
+  do {                                \
+    int s_ = (expr);                  \
+    if (s_ != SRT_OK) return s_;      \
+  } while (0)
+
+// One sparse operator in CSR form.  Entries are stored either as FP32 (v32)
+// or as BF16 bit patterns (v16); v64 holds the FP64 lengths when the plan was
+// built with SRT_KEEP_F64.
+struct SrtCsr {
+  int32_t rows = 0, cols = 0;
+  int64_t nnz = 0;
+  int32_t* rowptr = nullptr;  // rows + 1
+  int32_t* col = nullptr;     // nnz
+  float* v32 = nullptr;       // nnz (SRT_FP32)
+  uint16_t* v16 = nullptr;    // nnz (SRT_BF16)
+  double* v64 = nullptr;      // nnz (SRT_KEEP_F64)
+};
+
+struct srt_plan_s {
+  srt_geometry g;
+  int device = 0;
+  SrtCsr a1, a2, a1t, a2t;  // A1 = A^{1,2}, A2 = A^{3,4} and their transposes
+  int64_t dropped1 = 0, dropped2 = 0;
+  int64_t bytes = 0;
+  // per-stage timing (srt_plan_set_timing)
+  int timing = 0;
+  cudaEvent_t ev[2][5] = {};
+  int have_times[2] = {0, 0};
+};
+
+// ------------------------------------------------------------- assembly
+// Builds a1, a2, a1t, a2t of the plan (device kernels on `stream`).
+int srt_assemble(srt_plan_s* plan, cudaStream_t stream);
+void srt_csr_free(SrtCsr* m);
+
+// ------------------------------------------------------------- operators
+// y[b][r][n] = sum_e A[r, col[e]] * x[b][col[e]][n] for n < ncols.
+int srt_spmm(const SrtCsr& A, int weight_dtype, const float* x, int64_t ldx, int64_t bsx, float* y,
+             int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t stream);
+
+// out[b*obs + c*old + r] = in[b*ibs + r*ild + c] for r < rows, c < cols.
+int srt_transpose(const float* in, int64_t ild, int64_t ibs, float* out, int64_t old, int64_t obs,
+                  int rows, int cols, int batch, cudaStream_t stream);
+
+int srt_dot(const float* a, const float* b, int64_t n, double* out, double* partials,
+            cudaStream_t stream);
+constexpr int SRT_DOT_BLOCKS = 608;  // 152 SMs x 4
+
+// --------------------------------------------------- FP64 device helpers
+// Angle in [0, pi] whose cosine is u/r, clamped at the ends.  The sine side
+// is formed as sqrt((r-u)(r+u)) so tangency keeps full precision.
+__host__ __device__ inline double srt_acos_r(double u, double r) {
+  if (u >= r) return 0.0;
+  if (u <= -r) return SRT_PI;
+  return atan2(sqrt((r - u) * (r + u)), u);
+}
+
+// Angle in [-pi/2, pi/2] whose sine is u/r, clamped at the ends.
+__host__ __device__ inline double srt_asin_r(double u, double r) {
+  if (u >= r) return 0.5 * SRT_PI;
+  if (u <= -r) return -0.5 * SRT_PI;
+  return atan2(u, sqrt((r - u) * (r + u)));
+}
+
+__host__ __device__ inline double srt_overlap3(double a0, double a1, double b0, double b1, double c0,
+                                               double c1) {
+  double lo = fmax(a0, fmax(b0, c0));
+  double hi = fmin(a1, fmin(b1, c1));
+  return hi > lo ? hi - lo : 0.0;
+}
+
+// Exact length of the circle (cx, cy, r) inside the box [x0,x1] x [y0,y1].
+// On each quarter of the circle cos and sin are monotone, so the angles whose
+// x coordinate lies in [x0, x1] form one interval there, and likewise for y;
+// the arc measure is the sum over the quarters of the triple overlap.
+__host__ __device__ inline double srt_arc_in_rect(double cx, double cy, double r, double x0,
+                                                  double x1, double y0, double y1) {
+  const double hp = 0.5 * SRT_PI;
+  double a1 = srt_acos_r(x1 - cx, r), a0 = srt_acos_r(x0 - cx, r);  // x in box: [a1, a0] up
+  double s0 = srt_asin_r(y0 - cy, r), s1 = srt_asin_r(y1 - cy, r);  // y in box: [s0, s1] right
+  double t = srt_overlap3(0.0, hp, a1, a0, s0, s1);
+  t += srt_overlap3(hp, SRT_PI, a1, a0, SRT_PI - s1, SRT_PI - s0);
+  t += srt_overlap3(-SRT_PI, -hp, -a0, -a1, -SRT_PI - s1, -SRT_PI - s0);
+  t += srt_overlap3(-hp, 0.0, -a0, -a1, s0, s1);
+  return r * t;
+}
+
+// Round an FP64 value to BF16 (round to nearest, ties to even) in one step,
+// from the FP64 bit pattern: keep 7 fraction bits, round on the other 45.
+// Values below the BF16 normal range flush to signed zero (entries here are
+// lengths far above it).
+__host__ __device__ inline uint16_t srt_f64_to_bf16(double x) {
+#ifdef __CUDA_ARCH__
+  uint64_t b = (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t b;
+  memcpy(&b, &x, 8);
+#endif
+  uint64_t sign = b >> 63;
+  uint64_t mag = b & 0x7FFFFFFFFFFFFFFFull;
+  int e = (int)(mag >> 52) - 1023 + 127;
+  if (mag == 0 || e <= 0) return (uint16_t)(sign << 15);
+  if (e >= 255) return (uint16_t)((sign << 15) | 0x7F80u);
+  uint64_t frac = mag & ((1ull << 52) - 1);
+  uint64_t q = ((uint64_t)e << 7) | (frac >> 45);
+  uint64_t rem = frac & ((1ull << 45) - 1);
+  const uint64_t half = 1ull << 44;
+  if (rem > half || (rem == half && (q & 1))) q += 1;  // a carry moves into the exponent
+  return (uint16_t)((sign << 15) | q);
+}
+
+__device__ __forceinline__ float srt_bf16_to_f32(uint16_t v) {
+  return __uint_as_float(((uint32_t)v) << 16);
+}

@@ -1,0 +1,166 @@
+// Sparse-times-dense products of Algorithm 1 (A1 F, A2 Y) and Algorithm 2
+// (A2^T Y, A1^T F') of the paper, in gather form: every output row is owned by
+// one warp, so no atomics are used and results are deterministic.
+//
+// y[b][r][n] = sum_{e in row r} A[e] * x[b][col[e]][n],  n < ncols.
+// Lanes own consecutive dense columns (float4 when rows are 16-byte aligned);
+// a row's (column, value) pairs are loaded 32 at a time and broadcast with
+// warp shuffles.  Entries are FP32 or BF16; accumulation is FP32.
+#include "common.cuh"
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename V>
+__device__ __forceinline__ float wval(V v);
+template <>
+__device__ __forceinline__ float wval<float>(float v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float wval<uint16_t>(uint16_t v) {
+  return srt_bf16_to_f32(v);
+}
+
+// Vector path: each lane owns 4 consecutive columns of each 128-column chunk;
+// a warp covers CH chunks.  Requires ncols, ldx, ldy multiples of 4 and
+// 16-byte aligned bases.
+template <typename V, int CH>
+__global__ void __launch_bounds__(256) k_spmm_vec(int rows, const int32_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ col,
+                                                  const V* __restrict__ val,
+                                                  const float* __restrict__ x, int64_t ldx,
+                                                  int64_t bsx, float* __restrict__ y, int64_t ldy,
+                                                  int64_t bsy, int ncols) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  x += blockIdx.z * bsx;
+  y += blockIdx.z * bsy;
+  const int n0 = blockIdx.y * (128 * CH) + lane * 4;
+  float4 acc[CH];
+#pragma unroll
+  for (int q = 0; q < CH; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int e0 = rowptr[row], e1 = rowptr[row + 1];
+  for (int eb = e0; eb < e1; eb += 32) {
+    int c = 0;
+    float v = 0.f;
+    if (eb + lane < e1) {
+      c = col[eb + lane];
+      v = wval<V>(val[eb + lane]);
+    }
+    const int cnt = min(32, e1 - eb);
+    for (int i = 0; i < cnt; ++i) {
+      const int ci = __shfl_sync(FULL, c, i);
+      const float vi = __shfl_sync(FULL, v, i);
+      const float* xr = x + (int64_t)ci * ldx;
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int n = n0 + q * 128;
+        if (n < ncols) {
+          const float4 xv = __ldg(reinterpret_cast<const float4*>(xr + n));
+          acc[q].x = fmaf(vi, xv.x, acc[q].x);
+          acc[q].y = fmaf(vi, xv.y, acc[q].y);
+          acc[q].z = fmaf(vi, xv.z, acc[q].z);
+          acc[q].w = fmaf(vi, xv.w, acc[q].w);
+        }
+      }
+    }
+  }
+  float* yr = y + (int64_t)row * ldy;
+#pragma unroll
+  for (int q = 0; q < CH; ++q) {
+    const int n = n0 + q * 128;
+    if (n < ncols) *reinterpret_cast<float4*>(yr + n) = acc[q];
+  }
+}
+
+// Scalar path for any ncols / strides: lane owns columns lane + 32 i.
+template <typename V, int PER>
+__global__ void __launch_bounds__(256) k_spmm_scalar(int rows, const int32_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ col,
+                                                     const V* __restrict__ val,
+                                                     const float* __restrict__ x, int64_t ldx,
+                                                     int64_t bsx, float* __restrict__ y,
+                                                     int64_t ldy, int64_t bsy, int ncols) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (row >= rows) return;
+  x += blockIdx.z * bsx;
+  y += blockIdx.z * bsy;
+  const int n0 = blockIdx.y * (32 * PER) + lane;
+  float acc[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) acc[q] = 0.f;
+  const int e0 = rowptr[row], e1 = rowptr[row + 1];
+  for (int eb = e0; eb < e1; eb += 32) {
+    int c = 0;
+    float v = 0.f;
+    if (eb + lane < e1) {
+      c = col[eb + lane];
+      v = wval<V>(val[eb + lane]);
+    }
+    const int cnt = min(32, e1 - eb);
+    for (int i = 0; i < cnt; ++i) {
+      const int ci = __shfl_sync(FULL, c, i);
+      const float vi = __shfl_sync(FULL, v, i);
+      const float* xr = x + (int64_t)ci * ldx;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int n = n0 + q * 32;
+        if (n < ncols) acc[q] = fmaf(vi, __ldg(xr + n), acc[q]);
+      }
+    }
+  }
+  float* yr = y + (int64_t)row * ldy;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int n = n0 + q * 32;
+    if (n < ncols) yr[n] = acc[q];
+  }
+}
+
+template <typename V>
+int launch(const SrtCsr& A, const V* val, const float* x, int64_t ldx, int64_t bsx, float* y,
+           int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t st) {
+  const int rows_per_block = 8;
+  dim3 block(256);
+  const bool vec = (ncols % 4 == 0) && (ldx % 4 == 0) && (ldy % 4 == 0) && (bsx % 4 == 0) &&
+                   (bsy % 4 == 0) && ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0);
+  const int gx = (A.rows + rows_per_block - 1) / rows_per_block;
+  if (vec) {
+    const int chunks = (ncols + 127) / 128;
+    if (chunks >= 4) {
+      dim3 grid(gx, (ncols + 511) / 512, batch);
+      k_spmm_vec<V, 4><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
+                                               bsy, ncols);
+    } else if (chunks == 3) {
+      dim3 grid(gx, 1, batch);
+      k_spmm_vec<V, 3><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
+                                               bsy, ncols);
+    } else if (chunks == 2) {
+      dim3 grid(gx, 1, batch);
+      k_spmm_vec<V, 2><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
+                                               bsy, ncols);
+    } else {
+      dim3 grid(gx, 1, batch);
+      k_spmm_vec<V, 1><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
+                                               bsy, ncols);
+    }
+  } else {
+    dim3 grid(gx, (ncols + 127) / 128, batch);
+    k_spmm_scalar<V, 4><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
+                                                bsy, ncols);
+  }
+  SRT_CUDA_TRY(cudaGetLastError());
+  return SRT_OK;
+}
+
+}  // namespace
+
+int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx, float* y,
+             int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t st) {
+  if (wdt == SRT_BF16) return launch<uint16_t>(A, A.v16, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
+  return launch<float>(A, A.v32, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
+}

@@ -1,0 +1,87 @@
+"""GPU parity at the full workload sizes, on seeded samples the oracle can
+evaluate one by one (forward: sampled shells; adjoint: sampled voxels via the
+oracle's per-voxel weights), plus the adjoint identity on the whole output.
+
+srt256 runs in the launch configuration the benchmark times (batch 1, FP32
+entries) and in its BF16 form, on a phantom that is zero outside the central
+64^3 voxels (the full 256^3 oracle is out of reach: ~5e12 weight
+evaluations)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2402_15641_gb300 import inputs as I
+from tests.gpu_helpers import geom_pair, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def srt():
+    import torch
+    from paper_2402_15641_gb300 import build, srt as S
+    assert torch.cuda.is_available()
+    build.build()
+    return S
+
+
+def _samples(g, n_shells, n_vox, seed, crop=None):
+    rng = np.random.default_rng(seed)
+    sh = np.stack([rng.integers(0, g.n_phi, n_shells), rng.integers(0, g.n_zs, n_shells),
+                   rng.integers(0, g.n_ell, n_shells)], axis=1)
+    if crop is None:
+        vx = np.stack([rng.integers(0, g.ms, n_vox), rng.integers(0, g.ms, n_vox),
+                       rng.integers(0, g.mz, n_vox)], axis=1)
+    else:
+        a, b = (g.ms - crop) // 2, (g.mz - crop) // 2
+        vx = np.stack([rng.integers(a, a + crop, n_vox), rng.integers(a, a + crop, n_vox),
+                       rng.integers(b, b + crop, n_vox)], axis=1)
+    return sh, vx
+
+
+def _check(srt, orc, plan, o, f, y, sh, vx, tol):
+    p_gpu = to_np(plan.forward(to_dev(f)))
+    a_gpu = to_np(plan.adjoint(to_dev(y)))
+    want_p = orc.forward_shells(o, f, sh)
+    got_p = p_gpu[sh[:, 0], sh[:, 1], sh[:, 2]]
+    want_a = orc.adjoint_voxels(o, y, vx)
+    got_a = a_gpu[vx[:, 0], vx[:, 1], vx[:, 2]]
+    e_p, e_a = rel_l2(got_p, want_p), rel_l2(got_a, want_a)
+    assert e_p <= tol, e_p
+    assert e_a <= tol, e_a
+    return e_p, e_a
+
+
+def test_srt128_sampled(srt, orc):
+    sz = dict(I.sizes("srt128"))
+    g, o = geom_pair(orc, **sz)
+    plan = srt.Plan(g)
+    f = I.phantom("srt128")
+    y = I.probe("srt128")
+    sh, vx = _samples(g, 2048, 48, 31)
+    _check(srt, orc, plan, o, f, y, sh, vx, 1e-5)
+    fd, yd = to_dev(f), to_dev(y)
+    af, aty = plan.forward(fd), plan.adjoint(yd)
+    lhs, rhs = srt.dot_f64(af, yd), srt.dot_f64(fd, aty)
+    assert abs(lhs - rhs) / math.sqrt(srt.dot_f64(af, af) * srt.dot_f64(yd, yd)) <= 1e-6
+
+
+@pytest.fixture(scope="module")
+def srt256_inputs():
+    return I.crop_phantom("srt256", 64), I.probe("srt256")
+
+
+@pytest.mark.parametrize("wdt,tol", [("fp32", 1e-5), ("bf16", 5e-3)])
+def test_srt256_crop_sampled(srt, orc, srt256_inputs, wdt, tol):
+    sz = dict(I.sizes("srt256"))
+    g, o = geom_pair(orc, weight_dtype=wdt, **sz)
+    plan = srt.Plan(g)
+    f, y = srt256_inputs
+    sh, vx = _samples(g, 4096, 96, 41, crop=64)
+    e_p, e_a = _check(srt, orc, plan, o, f, y, sh, vx, tol)
+    print(f"srt256 {wdt}: forward rel-L2 {e_p:.3e}, adjoint rel-L2 {e_a:.3e}")
+    fd, yd = to_dev(f), to_dev(y)
+    af, aty = plan.forward(fd), plan.adjoint(yd)
+    lhs, rhs = srt.dot_f64(af, yd), srt.dot_f64(fd, aty)
+    assert abs(lhs - rhs) / math.sqrt(srt.dot_f64(af, af) * srt.dot_f64(yd, yd)) <= 1e-6

@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (stated for the workload in the benchmark spec and derived from
+the arithmetic): relative L2 <= 1e-5 for FP32-stored entries, <= 5e-3 for
+BF16-stored entries (FP32 accumulation in both), adjoint identity <= 1e-6
+relative in FP32.  Assembly entries are compared in FP64 before rounding
+(<= 1e-12 of the spacing per entry).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2402_15641_gb300 import inputs as I
+from tests.gpu_helpers import bf16_is_rne_of, geom_pair, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL, BF16_TOL, ADJ_TOL = 1e-5, 5e-3, 1e-6
+
+
+@pytest.fixture(scope="module")
+def srt():
+    import torch
+    from paper_2402_15641_gb300 import build, srt as S
+    assert torch.cuda.is_available()
+    build.build()
+    return S
+
+
+def _arcs_match(got_cols, got_vals, want: dict, scale):
+    got = dict(zip(got_cols.tolist(), got_vals.tolist()))
+    for k, v in want.items():
+        if k in got:
+            assert abs(got[k] - v) <= 1e-12 * scale, (k, got[k], v)
+        else:
+            assert v <= 1e-12 * scale, (k, v)  # dropped tangent touch
+    for k in got:
+        assert k in want, k
+
+
+TINY = dict(ms=5, mz=4, dxy=0.6, dz=0.45, radius=3.0, n_phi=6, n_zs=3, n_ell=12, phi0=0.37,
+            zs=(-0.7, 1.1))
+
+
+@pytest.mark.parametrize("sz", [TINY, dict(I.sizes("srt32"))])
+def test_assembly_entries_match_oracle_arcs(srt, orc, sz):
+    g, o = geom_pair(orc, keep_f64=True, **sz)
+    plan = srt.Plan(g)
+    rp, col, v32, v64 = plan.export(1, f64=True)
+    assert np.all(np.diff(rp) >= 0) and rp[-1] == len(col) == plan.info["nnz1"]
+    for r in range(g.n_phi * g.n_ell):
+        j, l = divmod(r, g.n_ell)
+        seg = slice(rp[r], rp[r + 1])
+        assert np.all(np.diff(col[seg]) > 0)
+        _arcs_match(col[seg], v64[seg], orc.circle_arcs(o, j, l), g.dxy)
+    np.testing.assert_array_equal(v32, v64.astype(np.float32))
+    rp, col, v32, v64 = plan.export(2, f64=True)
+    assert rp[-1] == plan.info["nnz2"]
+    for r in range(g.n_zs * g.n_ell):
+        h, m = divmod(r, g.n_ell)
+        seg = slice(rp[r], rp[r + 1])
+        assert np.all(np.diff(col[seg]) > 0)
+        _arcs_match(col[seg], v64[seg], orc.semicircle_arcs(o, h, m), g.dz)
+    np.testing.assert_array_equal(v32, v64.astype(np.float32))
+
+
+def test_transposes_are_exact(srt, orc):
+    import scipy.sparse as sp
+    g, _ = geom_pair(orc, **dict(I.sizes("srt32")), weight_dtype="bf16")
+    plan = srt.Plan(g)
+    for a, t, shape in ((1, 3, (plan.info["rows1"], plan.info["cols1"])),
+                        (2, 4, (plan.info["rows2"], plan.info["cols2"]))):
+        rp, col, val, _ = plan.export(a)
+        trp, tcol, tval, _ = plan.export(t)
+        A = sp.csr_matrix((val, col, rp), shape=shape)
+        AT = sp.csr_matrix((tval, tcol, trp), shape=shape[::-1])
+        want = A.T.tocsr()
+        want.sort_indices()
+        np.testing.assert_array_equal(AT.indptr, want.indptr)
+        np.testing.assert_array_equal(AT.indices, want.indices)
+        np.testing.assert_array_equal(AT.data.view(np.uint32), want.data.view(np.uint32))
+
+
+def test_bf16_entries_are_rne_of_fp64(srt, orc):
+    g, _ = geom_pair(orc, **dict(I.sizes("srt32")), weight_dtype="bf16", keep_f64=True)
+    plan = srt.Plan(g)
+    for which in (1, 2, 3, 4):
+        _, _, v, v64 = plan.export(which, f64=True)
+        assert np.all(bf16_is_rne_of(v, v64))
+
+
+@pytest.fixture(scope="module")
+def c0(orc):
+    sz = dict(I.sizes("srt32"))
+    _, o = geom_pair(orc, **sz)
+    f = I.phantom("srt32")
+    g = I.probe("srt32")
+    return sz, f, g, orc.forward(o, f), orc.adjoint(o, g)
+
+
+@pytest.mark.parametrize("wdt,tol", [("fp32", FP32_TOL), ("bf16", BF16_TOL)])
+def test_forward_adjoint_c0(srt, orc, c0, wdt, tol):
+    sz, f, y, pf, fa = c0
+    g, _ = geom_pair(orc, weight_dtype=wdt, **sz)
+    plan = srt.Plan(g)
+    p_gpu = to_np(plan.forward(to_dev(f)))
+    f_gpu = to_np(plan.adjoint(to_dev(y)))
+    assert rel_l2(p_gpu, pf) <= tol
+    assert rel_l2(f_gpu, fa) <= tol
+    if wdt == "fp32":  # the BF16 error is large enough to be seen at all
+        return
+    assert rel_l2(p_gpu, pf) > 1e-5
+
+
+@pytest.mark.parametrize("name", ["srt32", "srt16fd"])
+def test_adjoint_identity_on_gpu(srt, orc, name):
+    sz = dict(I.sizes(name))
+    g, _ = geom_pair(orc, **sz)
+    plan = srt.Plan(g)
+    f = to_dev(I.phantom(name))
+    y = to_dev(I.probe(name))
+    af = plan.forward(f)
+    aty = plan.adjoint(y)
+    lhs = srt.dot_f64(af, y)
+    rhs = srt.dot_f64(f, aty)
+    nrm = math.sqrt(srt.dot_f64(af, af) * srt.dot_f64(y, y))
+    assert abs(lhs - rhs) / nrm <= ADJ_TOL
+    # the FP64 device dot agrees with a host FP64 dot of the same floats
+    assert lhs == pytest.approx(float(np.dot(to_np(af).ravel(), to_np(y).ravel())), rel=1e-12)
+
+
+RAGGED = [
+    dict(ms=7, mz=5, dxy=0.5, dz=0.37, radius=6.0, n_phi=6, n_zs=3, n_ell=13, phi0=0.2),
+    dict(ms=9, mz=3, dxy=0.3, dz=0.8, radius=2.5, n_phi=5, n_zs=7, n_ell=31, zs=(-2.0, 1.5)),
+    dict(ms=16, mz=12, dxy=0.5, dz=0.5, radius=12.0, n_phi=32, n_zs=16, n_ell=48),
+    dict(ms=1, mz=1, dxy=1.0, dz=1.0, radius=2.0, n_phi=1, n_zs=1, n_ell=2),
+    dict(ms=20, mz=36, dxy=0.4, dz=0.25, radius=9.0, n_phi=12, n_zs=40, n_ell=57, phi0=1.1),
+]
+
+
+@pytest.mark.parametrize("sz", RAGGED)
+@pytest.mark.parametrize("batch", [1, 3])
+def test_ragged_geometries_full(srt, orc, sz, batch):
+    g, o = geom_pair(orc, **sz)
+    plan = srt.Plan(g)
+    rng = np.random.default_rng(7)
+    f = rng.uniform(0, 1, (batch, *g.f_shape))
+    y = rng.standard_normal((batch, *g.p_shape))
+    pf = np.stack([orc.forward(o, f[b]) for b in range(batch)])
+    fa = np.stack([orc.adjoint(o, y[b]) for b in range(batch)])
+    assert rel_l2(to_np(plan.forward(to_dev(f))), pf) <= FP32_TOL
+    assert rel_l2(to_np(plan.adjoint(to_dev(y))), fa) <= FP32_TOL
+
+
+def test_fd16_full_and_batched_bitwise(srt, orc):
+    import torch
+    sz = dict(I.sizes("srt16fd"))
+    g, o = geom_pair(orc, **sz)
+    plan = srt.Plan(g)
+    rng = np.random.default_rng(8)
+    f = rng.uniform(0, 1, (4, *g.f_shape))
+    y = rng.standard_normal((4, *g.p_shape))
+    pb = plan.forward(to_dev(f))
+    ab = plan.adjoint(to_dev(y))
+    for b in range(4):
+        assert torch.equal(plan.forward(to_dev(f[b])), pb[b])
+        assert torch.equal(plan.adjoint(to_dev(y[b])), ab[b])
+    assert rel_l2(to_np(pb[2]), orc.forward(o, f[2])) <= FP32_TOL
+    assert rel_l2(to_np(ab[1]), orc.adjoint(o, y[1])) <= FP32_TOL
+
+
+def test_host_buffer_variants_equal_device(srt, orc):
+    import torch
+    g, _ = geom_pair(orc, **dict(I.sizes("srt16fd")))
+    plan = srt.Plan(g)
+    rng = np.random.default_rng(9)
+    f = torch.from_numpy(rng.uniform(0, 1, (2, *g.f_shape)).astype(np.float32)).pin_memory()
+    y = torch.from_numpy(rng.standard_normal((2, *g.p_shape)).astype(np.float32)).pin_memory()
+    p_h = torch.empty((2, *g.p_shape), dtype=torch.float32).pin_memory()
+    f_h = torch.empty((2, *g.f_shape), dtype=torch.float32).pin_memory()
+    plan.forward_host(f, p_h)
+    plan.adjoint_host(y, f_h)
+    assert torch.equal(p_h, plan.forward(f.cuda()).cpu())
+    assert torch.equal(f_h, plan.adjoint(y.cuda()).cpu())
+
+
+def test_workspace_and_argument_errors(srt, orc):
+    import torch
+    from paper_2402_15641_gb300._lib import SrtError, SRT_ERR_WORKSPACE, SRT_ERR_ARG
+    g, _ = geom_pair(orc, **dict(I.sizes("srt16fd")))
+    plan = srt.Plan(g)
+    f = torch.zeros(g.f_shape, device="cuda")
+    small = torch.empty(plan.workspace_bytes(1) - 256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(SrtError) as e:
+        plan.forward(f, workspace=small)
+    assert e.value.code == SRT_ERR_WORKSPACE
+    big = torch.empty(plan.workspace_bytes(1) + 512, dtype=torch.uint8, device="cuda")
+    with pytest.raises(SrtError) as e:
+        plan.forward(f, workspace=big[4:])  # misaligned
+    assert e.value.code == SRT_ERR_WORKSPACE
+    with pytest.raises(SrtError) as e:  # batch 2 does not fit a batch-1 workspace
+        plan.forward(torch.zeros((2, *g.f_shape), device="cuda"), workspace=plan.workspace(1))
+    assert e.value.code == SRT_ERR_WORKSPACE
+    raw = torch.zeros(g.ms * g.ms * g.mz + 4, device="cuda")
+    ws = plan.workspace(1)
+    rc = plan._lib.srt_forward(plan._h, raw[1:].data_ptr(), raw.data_ptr(), 1, ws.data_ptr(),
+                               ws.numel(), None)  # misaligned volume pointer
+    assert rc == SRT_ERR_ARG
+
+
+def test_plan_info_and_timing(srt, orc):
+    import torch
+    g, _ = geom_pair(orc, **dict(I.sizes("srt32")))
+    plan = srt.Plan(g)
+    inf = plan.info
+    assert inf["rows1"] == 64 * 96 and inf["cols1"] == 32 * 32
+    assert inf["rows2"] == 32 * 96 and inf["cols2"] == 96 * 32
+    assert inf["nnz1"] > 0 and inf["nnz2"] > 0 and inf["device_bytes"] > 0
+    plan.set_timing(True)
+    f = to_dev(I.phantom("srt32"))
+    plan.forward(f)
+    t = plan.stage_times(0)
+    assert len(t) == 4 and all(x >= 0 for x in t)
+    from paper_2402_15641_gb300._lib import SrtError
+    with pytest.raises(SrtError):
+        plan.stage_times(1)
+    assert plan.launches_per_call(0) == 4
+    torch.cuda.synchronize()
