@@ -1,0 +1,442 @@
+#!/usr/bin/env python
+"""Throughput of the cylindrical-aperture SRT: forward + matched adjoint.
+
+One step = srt_forward followed by srt_adjoint of one batch of volumes on the
+256^3 workload (256^3 voxels @ 0.1 mm, R = 20 mm, 256 sensor columns, 256
+rings, 768 radius bins; FP32 entries, batch 1) unless --workload/--weights
+say otherwise.  Inputs are seeded synthetic phantoms (100 balls + 500-blob
+vessel tree) and N(0, 1) measurement-shaped data, resident in HBM before the
+timed region; L2 is flushed (256 MiB write) between timed steps.
+
+Prints ONE JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle
+(the only reference this method has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SRT fwd+adj ops/s & HBM GB/s vs peak at 256^3"
+UNIT = "fwd+adj pairs/s"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="srt256")
+    p.add_argument("--weights", choices=["fp32", "bf16"], default="fp32")
+    p.add_argument("--batch", type=int, default=1)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    d = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+    hbm = d.get("hbm_gbs", 6800.0)
+    sm_max = d.get("sm_max_mhz", 2070.0)
+    src = "measured" if "hbm_gbs" in d else "fallback"
+    # FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128
+    # FP32 lanes x 2 FLOP per FMA x clock.
+    fp32 = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    return dict(hbm_gbs=hbm, fp32_tflops=fp32, sm_max_mhz=sm_max, src=src)
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.file.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2402_15641_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, n), "rb") as fh:
+                h.update(n.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_stage, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as fh:
+        for line in fh:
+            line = line.strip()
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                rec[k.strip()] = v.strip()
+    if rec.get("csrc_sha") != csrc_digest():
+        return None
+    v = rec.get(f"dram_bytes_per_launch.{kernel_stage}")
+    return float(v) if v else None
+
+
+def stage_model(geom, info, batch, weights):
+    """Algorithmic FLOPs and compulsory bytes per launch of each stage."""
+    vb = 2 if weights == "bf16" else 4
+    pix, c1 = geom.ms * geom.ms, geom.n_ell * geom.mz
+    r1, r2 = geom.n_phi * geom.n_ell, geom.n_zs * geom.n_ell
+    nnz1, nnz2 = info["nnz1"], info["nnz2"]
+    y1 = 4 * batch * r1 * geom.mz           # bytes of Y1 (= Y1')
+    pp = 4 * batch * r2 * geom.n_phi        # bytes of P' (= p)
+    fv = 4 * batch * pix * geom.mz          # bytes of f
+    spmm1 = dict(flop=2 * nnz1 * geom.mz * batch,
+                 bytes=nnz1 * (vb + 4) + 4 * (r1 + 1) + fv + y1)
+    spmm2 = dict(flop=2 * nnz2 * geom.n_phi * batch,
+                 bytes=nnz2 * (vb + 4) + 4 * (r2 + 1) + y1 + pp)
+    spmm2t = dict(flop=spmm2["flop"], bytes=nnz2 * (vb + 4) + 4 * (c1 + 1) + pp + y1)
+    spmm1t = dict(flop=spmm1["flop"], bytes=nnz1 * (vb + 4) + 4 * (pix + 1) + y1 + fv)
+    p1 = dict(flop=0, bytes=2 * y1)
+    p2 = dict(flop=0, bytes=2 * pp)
+    return {"fwd": [("spmm1", spmm1), ("permute1", p1), ("spmm2", spmm2), ("permute2", p2)],
+            "adj": [("permute2_inv", p2), ("spmm2t", spmm2t), ("permute1_inv", p1),
+                    ("spmm1t", spmm1t)]}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_config(name, geom, batch, weights, extra=None):
+    from paper_2402_15641_gb300 import inputs as I
+    w = I.WORKLOADS[name]
+    cfg = {"workload": f"{name}: {geom.ms}^2x{geom.mz} voxels @ {geom.dxy} mm, R={geom.radius} mm, "
+                       f"n_phi={geom.n_phi}, n_zs={geom.n_zs}, n_ell={geom.n_ell}, "
+                       f"{weights} entries, batch {batch}",
+           "phantom": f"{w.get('n_balls', 0)} balls + {w.get('n_blobs', 0)}-blob vessel tree "
+                      f"(seed 0); adjoint input N(0,1) (seed 1)",
+           "batch": batch, "weights": weights}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def cpu_oracle_rate(name, budget_s, seed=5):
+    """Oracle forward + adjoint on a seeded shell sample sized to budget_s;
+    returns (pairs/s extrapolated to the full workload, threads, sample text)."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2402_15641_gb300 import inputs as I
+    sz = I.sizes(name)
+    g = O.OracleGeometry.default(**sz)
+    f = I.phantom(name)
+    y = I.probe(name)
+    total = g.n_phi * g.n_zs * g.n_ell
+    rng = np.random.default_rng(seed)
+
+    def sample(n):
+        return np.stack([rng.integers(0, g.n_phi, n), rng.integers(0, g.n_zs, n),
+                         rng.integers(0, g.n_ell, n)], axis=1)
+
+    def run(sh):
+        t0 = time.perf_counter()
+        O.forward_shells(g, f, sh)
+        O.adjoint_shells(g, sh, y[sh[:, 0], sh[:, 1], sh[:, 2]])
+        return time.perf_counter() - t0
+
+    n0 = 64
+    t0 = run(sample(n0))
+    n = max(n0, int(n0 * budget_s / max(t0, 1e-3)))
+    t = run(sample(n))
+    rate = (n / total) / t
+    return rate, O.num_threads(), n, t
+
+
+def run_reference(args):
+    world, rank, _ = dist_init()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_2402_15641_gb300 import inputs as I
+    import numpy as np
+    sz = I.sizes(args.workload)
+    g = O.OracleGeometry.default(**sz)
+    f = I.phantom(args.workload)
+    y = I.probe(args.workload)
+    total = g.n_phi * g.n_zs * g.n_ell
+    rng = np.random.default_rng(11)
+    # size each step so that warmup + steps take about 90 s of host time
+    sh = np.stack([rng.integers(0, g.n_phi, 64), rng.integers(0, g.n_zs, 64),
+                   rng.integers(0, g.n_ell, 64)], axis=1)
+    t0 = time.perf_counter()
+    O.forward_shells(g, f, sh)
+    O.adjoint_shells(g, sh, y[sh[:, 0], sh[:, 1], sh[:, 2]])
+    per_shell = (time.perf_counter() - t0) / 64
+    per_step = 90.0 / max(1, args.steps + args.warmup)
+    n = int(max(8, min(200000, per_step / per_shell)))
+    times = []
+    for it in range(args.warmup + args.steps):
+        sh = np.stack([rng.integers(0, g.n_phi, n), rng.integers(0, g.n_zs, n),
+                       rng.integers(0, g.n_ell, n)], axis=1)
+        t0 = time.perf_counter()
+        O.forward_shells(g, f, sh)
+        O.adjoint_shells(g, sh, y[sh[:, 0], sh[:, 1], sh[:, 2]])
+        if it >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    frac = n / total
+    value = args.steps * frac / sum(times)
+    sample = (f"{n} seeded shells (of {total}) per step, oracle forward + adjoint over them; "
+              f"rate extrapolated to the full operator by shell count")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.workload} (FP64 CPU oracle, per-shell quadrature)",
+                      "sample_shells_per_step": n},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2402_15641_gb300 import build, inputs as I
+    from paper_2402_15641_gb300.srt import Geometry, Plan
+
+    build.build()
+    pk = peaks()
+    sz = I.sizes(args.workload)
+    geom = Geometry.from_sizes(sz, weight_dtype=args.weights)
+    B = args.batch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = Plan(geom)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+
+    f_np = I.phantom(args.workload).astype(np.float32)
+    y_np = I.probe(args.workload).astype(np.float32)
+    f = torch.from_numpy(np.broadcast_to(f_np, (B, *f_np.shape)).copy()).cuda()
+    y = torch.from_numpy(np.broadcast_to(y_np, (B, *y_np.shape)).copy()).cuda()
+    p_out = torch.empty((B, *geom.p_shape), device="cuda")
+    f_out = torch.empty((B, *geom.f_shape), device="cuda")
+    ws = plan.workspace(B)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.forward(f, out=p_out, workspace=ws)
+        plan.adjoint(y, out=f_out, workspace=ws)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    plan.set_timing(True)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stage = {"fwd": [], "adj": []}
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        plan.forward(f, out=p_out, workspace=ws)
+        plan.adjoint(y, out=f_out, workspace=ws)
+        ev[k][1].record(stream)
+        stage["fwd"].append(plan.stage_times(0))  # both calls are queued: no sync inside a step
+        stage["adj"].append(plan.stage_times(1))
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    plan.set_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = reduce_max(sum(step_ms), world)
+    value = world * args.steps * B / (total_ms / 1e3)
+
+    # per-stage figures from the CUDA events recorded on the launch stream
+    model = stage_model(geom, plan.info, B, args.weights)
+    stages = {}
+    for d in ("fwd", "adj"):
+        mean = np.mean(np.array(stage[d]), axis=0)
+        for (name, m), ms in zip(model[d], mean):
+            s = {"ms": round(float(ms), 5), "gb_s": round(m["bytes"] / (ms * 1e6), 1),
+                 "hbm_frac": round(m["bytes"] / (ms * 1e6) / pk["hbm_gbs"], 4)}
+            if m["flop"]:
+                s["tflop_s"] = round(m["flop"] / (ms * 1e9), 3)
+                s["fp32_frac"] = round(m["flop"] / (ms * 1e9) / pk["fp32_tflops"], 4)
+            s["flop"], s["bytes"] = m["flop"], m["bytes"]
+            stages[f"{d}.{name}"] = s
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    ds = stages[dom]
+    if "tflop_s" in ds:
+        roof = {"bound": "alu", "achieved": ds["tflop_s"], "peak": round(pk["fp32_tflops"], 2),
+                "unit": "TFLOP/s", "frac": ds["fp32_frac"],
+                "traffic": ncu_traffic(dom, args.workload), "kernel": dom,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock "
+                               f"{pk['sm_max_mhz']:.0f} MHz"}
+    else:
+        roof = {"bound": "hbm", "achieved": ds["gb_s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ds["hbm_frac"], "traffic": ncu_traffic(dom, args.workload),
+                "kernel": dom, "peak_source": f"{pk['src']} (MEASURED_PEAKS.json hbm_gbs)"}
+    step_bytes = sum(s["bytes"] for s in stages.values())
+    hbm = {"algorithmic_gb_per_step": round(step_bytes / 1e9, 4),
+           "gb_s": round(step_bytes / (total_ms / args.steps * 1e6), 1)}
+    hbm["frac_of_peak"] = round(hbm["gb_s"] / pk["hbm_gbs"], 4)
+
+    # end to end through the public host-buffer entry points
+    e2e = None
+    if args.e2e_steps > 0:
+        f_h = torch.from_numpy(np.broadcast_to(f_np, (B, *f_np.shape)).copy()).pin_memory()
+        y_h = torch.from_numpy(np.broadcast_to(y_np, (B, *y_np.shape)).copy()).pin_memory()
+        p_h = torch.empty((B, *geom.p_shape), dtype=torch.float32).pin_memory()
+        a_h = torch.empty((B, *geom.f_shape), dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            plan.forward_host(f_h, p_h)
+            plan.adjoint_host(y_h, a_h)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.forward_host(f_h, p_h)
+            plan.adjoint_host(y_h, a_h)
+            _ = float(p_h[0, 0, 0, 0]) + float(a_h[0, 0, 0, 0])
+        e2e_s = reduce_max(time.perf_counter() - t0, world)
+        e2e = {"value": world * args.e2e_steps * B / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": f_h.numel() * 4 + y_h.numel() * 4,
+               "d2h_bytes_per_step": p_h.numel() * 4 + a_h.numel() * 4,
+               "steps": args.e2e_steps}
+
+    launches = args.steps * (plan.launches_per_call(0, B) + plan.launches_per_call(1, B))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded phantoms and N(0,1) data, no dataset)",
+           "config": workload_config(args.workload, geom, B, args.weights,
+                                     {"l2": "flushed between steps (256 MiB write, untimed)",
+                                      "parallelism": "replicas" if world > 1 else "single GPU",
+                                      "plan_build_s": round(plan_s, 3),
+                                      "nnz1": plan.info["nnz1"], "nnz2": plan.info["nnz2"]}),
+           "roofline": roof, "hbm": hbm, "stages": stages, "clocks": clk, "e2e": e2e,
+           "gpu_launches": launches}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, n, t = cpu_oracle_rate(args.workload, 15.0)
+        out["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle forward + adjoint over {n} seeded shells of "
+                      f"{geom.n_phi * geom.n_zs * geom.n_ell} ({t:.1f} s); rate extrapolated "
+                      f"to the full operator by shell count"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -47,6 +47,8 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
 
 /* Plan flags. */
 #define SRT_KEEP_F64 0x1 /* keep FP64 copies of A1/A2 entries for srt_plan_export */
+#define SRT_CSR_ONLY 0x2 /* apply every product from plain CSR                       */
+#define SRT_TOEPLITZ 0x4 /* second stage as a z-correlation (rings at slab centres) */
 
 /*
  * Geometry (Sec. 3.1, Algorithm 1 inputs).  Lengths in mm, angles in rad.

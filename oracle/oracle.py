@@ -115,6 +115,7 @@ def lib():
         _lib.orc_adjoint.argtypes = [G, dp, dp, ctypes.c_int]
         _lib.orc_forward_shells.argtypes = [G, dp, ip, ctypes.c_long, dp, ctypes.c_int]
         _lib.orc_adjoint_voxels.argtypes = [G, dp, ip, ctypes.c_long, dp, ctypes.c_int]
+        _lib.orc_adjoint_shells.argtypes = [G, ip, dp, ctypes.c_long, dp, ctypes.c_int]
         _lib.orc_shell_contrib.argtypes = [G, ctypes.c_int, ctypes.c_int, ctypes.c_int, lp, dp,
                                            ctypes.c_long]
         _lib.orc_shell_contrib.restype = ctypes.c_long
@@ -182,6 +183,19 @@ def adjoint_voxels(g: OracleGeometry, p, voxels, nthreads: int = 0) -> np.ndarra
     if r:
         raise RuntimeError(f"orc_adjoint_voxels failed ({r})")
     return out
+
+
+def adjoint_shells(g: OracleGeometry, shells, vals, nthreads: int = 0) -> np.ndarray:
+    """A^T applied to data that is zero except at shells[i] = (j, h, m), where
+    it equals vals[i]; returns the full volume."""
+    sh = np.ascontiguousarray(shells, dtype=np.int32).reshape(-1, 3)
+    v = np.ascontiguousarray(vals, dtype=np.float64).reshape(-1)
+    f = np.zeros(g.f_shape, dtype=np.float64)
+    r = lib().orc_adjoint_shells(ctypes.byref(_cg(g)), _iptr(sh), _dptr(v), len(sh), _dptr(f),
+                                 nthreads)
+    if r:
+        raise RuntimeError(f"orc_adjoint_shells failed ({r})")
+    return f
 
 
 def shell_weights(g: OracleGeometry, j: int, h: int, m: int) -> dict:

@@ -171,8 +171,8 @@ static int circle_walk(const orc_geom* g, double sx, double sy, double rho, doub
  * elementary contribution; voxel = (ix*ms + iy)*mz + k.                  */
 typedef void (*emit_fn)(void* ctx, long voxel, double weight);
 
-static void shell_walk(const orc_geom* g, orc_ws* w, int j, int h, int m, emit_fn emit,
-                       void* ctx) {
+static void shell_walk_k(const orc_geom* g, orc_ws* w, int j, int h, int m, int k_lo, int k_hi,
+                         emit_fn emit, void* ctx) {
   const double hz = half_z(g), dl = dell(g);
   const double ell = ell_centre(g, m), zc = ring_z(g, h);
   const double sx = sensor_x(g, j), sy = sensor_y(g, j);
@@ -201,7 +201,7 @@ static void shell_walk(const orc_geom* g, orc_ws* w, int j, int h, int m, emit_f
     double z = zc + ell * cos(tm), rho = ell * sin(tm);
     int k = (int)floor((z + hz) / g->dz);
     int l = (int)floor((rho - g->ell_lo) / dl);
-    if (k < 0 || k >= g->mz || l < 0 || l >= g->n_ell) continue;
+    if (k < k_lo || k >= k_hi || l < 0 || l >= g->n_ell) continue;
     double wt = ell * (t1 - t0); /* arc length in the (z, rho) plane */
     if (l != w->cl) {            /* in-plane circle for bin l, radius rho_l */
       w->cn = circle_walk(g, sx, sy, ell_centre(g, l), w->ab, w->cpix, w->clen);
@@ -210,6 +210,11 @@ static void shell_walk(const orc_geom* g, orc_ws* w, int j, int h, int m, emit_f
     for (int q = 0; q < w->cn; ++q)
       emit(ctx, (long)w->cpix[q] * g->mz + k, wt * w->clen[q]);
   }
+}
+
+static void shell_walk(const orc_geom* g, orc_ws* w, int j, int h, int m, emit_fn emit,
+                       void* ctx) {
+  shell_walk_k(g, w, j, h, m, 0, g->mz, emit, ctx);
 }
 
 /* ------------------------------------------------------- callbacks */
@@ -359,6 +364,41 @@ int orc_adjoint(const orc_geom* g, const double* p, double* f, int nthreads) {
     f[v] = a;
   }
   free(buf);
+  return err;
+}
+
+/* Adjoint restricted to a list of shells: f[voxel] += sum_i vals[i] *
+ * weight(shell_i, voxel).  Each thread owns a range of slabs and walks every
+ * listed shell, keeping only its own slabs, so the sums are deterministic and
+ * no per-thread volume copies are needed.  f must be zeroed by the caller. */
+int orc_adjoint_shells(const orc_geom* g, const int32_t* shells, const double* vals, long n,
+                       double* f, int nthreads) {
+  if (check_geom(g)) return -1;
+  set_threads(nthreads);
+  int err = 0;
+#pragma omp parallel
+  {
+    int nt = 1, tid = 0;
+#ifdef _OPENMP
+    nt = omp_get_num_threads();
+    tid = omp_get_thread_num();
+#endif
+    int k_lo = (int)((long)g->mz * tid / nt), k_hi = (int)((long)g->mz * (tid + 1) / nt);
+    orc_ws w;
+    if (ws_init(&w, g)) {
+#pragma omp atomic write
+      err = -2;
+    } else if (k_hi > k_lo) {
+      adj_ctx c = {f, 0.0};
+      for (long i = 0; i < n; ++i) {
+        c.gval = vals[i];
+        if (c.gval != 0.0)
+          shell_walk_k(g, &w, shells[3 * i], shells[3 * i + 1], shells[3 * i + 2], k_lo, k_hi,
+                       emit_adj, &c);
+      }
+    }
+    ws_free(&w);
+  }
   return err;
 }
 

@@ -15,6 +15,8 @@ SRT_OK, SRT_ERR_ARG, SRT_ERR_GEOMETRY, SRT_ERR_OOM, SRT_ERR_CUDA = 0, 1, 2, 3, 4
 SRT_ERR_WORKSPACE, SRT_ERR_TIMEOUT, SRT_ERR_NOT_READY = 5, 6, 7
 SRT_FP32, SRT_BF16 = 0, 1
 SRT_KEEP_F64 = 1
+SRT_CSR_ONLY = 2
+SRT_TOEPLITZ = 4
 
 
 class SrtGeometry(ctypes.Structure):

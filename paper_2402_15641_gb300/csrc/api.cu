@@ -20,11 +20,14 @@ inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline int64_t align256(int64_t b) { return (b + 255) & ~(int64_t)255; }
 
-// Elements of one intermediate buffer: max(|Y1|, |P'|) over the batch.
+// Elements of one intermediate buffer: the largest of Y1, P' and the tiled
+// slabs of the second stage, whose dense columns are padded to a multiple of
+// SRT_TOEP_NC.
 int64_t buf_elems(const srt_geometry& g, int batch) {
-  const int64_t y1 = (int64_t)batch * g.n_phi * g.n_ell * g.mz;
-  const int64_t pp = (int64_t)batch * g.n_phi * g.n_zs * g.n_ell;
-  return y1 > pp ? y1 : pp;
+  const int64_t nb = (int64_t)batch * g.n_phi;
+  const int64_t nb4 = (nb + SRT_TOEP_NC - 1) / SRT_TOEP_NC * SRT_TOEP_NC;
+  const int64_t zmax = g.mz > g.n_zs ? g.mz : g.n_zs;
+  return nb4 * g.n_ell * zmax;
 }
 
 int check_geometry(const srt_geometry& g) {
@@ -49,6 +52,8 @@ void free_plan(srt_plan_s* p) {
   srt_csr_free(&p->a2);
   srt_csr_free(&p->a1t);
   srt_csr_free(&p->a2t);
+  srt_taps_free(&p->tf);
+  srt_taps_free(&p->ta);
   for (int d = 0; d < 2; ++d)
     for (int i = 0; i < 5; ++i)
       if (p->ev[d][i]) cudaEventDestroy(p->ev[d][i]);
@@ -72,13 +77,24 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
   const int64_t nb = (int64_t)B * g.n_phi;  // dense width of the second stage
   mark(p, 0, 0, st);
+  // Y1[b][j][l][k] = A1 F_b (CRT in the first plane, all slabs at once)
   SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B, st));
   mark(p, 0, 1, st);
-  SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
-  mark(p, 0, 2, st);
-  SRT_TRY(srt_spmm(p->a2, g.weight_dtype, w1, nb, 0, w0, nb, 0, (int)nb, 1, st));
-  mark(p, 0, 3, st);
-  SRT_TRY(srt_transpose(w0, nb, g.n_phi, out, r2, (int64_t)g.n_phi * r2, (int)r2, g.n_phi, B, st));
+  if (p->toeplitz) {
+    // slabs Y1'[l][z][n] in tiles, then the vertical CRT as a z-correlation
+    // written straight into p[b][j][h][m]
+    SRT_TRY(srt_tiles_from_rows(w0, g.n_ell, g.mz, (int)nb, w1, st));
+    mark(p, 0, 2, st);
+    SRT_TRY(srt_toep_apply(p->tf, g.weight_dtype, g.mz, g.mz - 1, g.n_ell, (int)nb, w1, out,
+                           r2, g.n_ell, 1, st));
+    mark(p, 0, 3, st);
+  } else {
+    SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
+    mark(p, 0, 2, st);
+    SRT_TRY(srt_spmm(p->a2, g.weight_dtype, w1, nb, 0, w0, nb, 0, (int)nb, 1, st));
+    mark(p, 0, 3, st);
+    SRT_TRY(srt_transpose(w0, nb, g.n_phi, out, r2, (int64_t)g.n_phi * r2, (int)r2, g.n_phi, B, st));
+  }
   mark(p, 0, 4, st);
   if (p->timing) p->have_times[0] = 1;
   return SRT_OK;
@@ -91,13 +107,26 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
   const int64_t nb = (int64_t)B * g.n_phi;
   mark(p, 1, 0, st);
-  SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
-  mark(p, 1, 1, st);
-  SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));
-  mark(p, 1, 2, st);
-  SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
+  const float* f1;  // F1[b][j][l][k], input of A1^T
+  if (p->toeplitz) {
+    // slabs P'[m][h][n] in tiles, then A2^T as a z-correlation written
+    // straight into F1[b][j][l][k]
+    SRT_TRY(srt_tiles_from_cols(in, g.n_ell, g.n_zs, (int)nb, w0, st));
+    mark(p, 1, 1, st);
+    SRT_TRY(srt_toep_apply(p->ta, g.weight_dtype, g.mz, g.mz - 1, g.n_ell, (int)nb, w0, w1,
+                           c1, 1, g.mz, st));
+    mark(p, 1, 2, st);
+    f1 = w1;
+  } else {
+    SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
+    mark(p, 1, 1, st);
+    SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));
+    mark(p, 1, 2, st);
+    SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
+    f1 = w0;
+  }
   mark(p, 1, 3, st);
-  SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, w0, g.mz, r1 * g.mz, f, g.mz, pix * g.mz, g.mz, B, st));
+  SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f, g.mz, pix * g.mz, g.mz, B, st));
   mark(p, 1, 4, st);
   if (p->timing) p->have_times[1] = 1;
   return SRT_OK;
@@ -304,7 +333,8 @@ int srt_stage_times(srt_plan_t p, int32_t dir, float* ms, int32_t n) {
 int srt_launches_per_call(srt_plan_t p, int32_t dir, int32_t batch) {
   (void)dir;
   (void)batch;
-  return p ? 4 : 0;
+  if (!p) return 0;
+  return p->toeplitz ? 3 : 4;
 }
 
 int srt_plan_destroy(srt_plan_t p) {

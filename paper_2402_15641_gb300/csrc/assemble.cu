@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "devutil.cuh"
 
 namespace {
 
@@ -187,6 +188,53 @@ __global__ void __launch_bounds__(256) k_assemble(GeomDev G, int rows, int pass,
   }
 }
 
+// Expand the master tensor T (one ring at z = 0 on a doubled slab grid: rows m,
+// columns l*(2 mz - 1) + k2, offset d = k2 - (mz - 1)) into A2's rows (h, m):
+// entry (l, h + d) when 0 <= h + d < mz.  One warp per row; order and values
+// are kept, so A2 holds T's entries bitwise.
+__global__ void __launch_bounds__(256) k_expand_toeplitz(int mz, int n_ell, int rows, int pass,
+                                                         const int32_t* __restrict__ tptr,
+                                                         const int32_t* __restrict__ tcol,
+                                                         const float* __restrict__ t32,
+                                                         const uint16_t* __restrict__ t16,
+                                                         const double* __restrict__ t64,
+                                                         int32_t* __restrict__ counts,
+                                                         const int32_t* __restrict__ rowptr,
+                                                         int32_t* __restrict__ col,
+                                                         float* __restrict__ v32,
+                                                         uint16_t* __restrict__ v16,
+                                                         double* __restrict__ v64) {
+  const int lane = threadIdx.x & 31;
+  const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  if (row >= rows) return;
+  const int h = row / n_ell, m = row % n_ell;
+  const int mz2 = 2 * mz - 1;
+  const int e0 = tptr[m], e1 = tptr[m + 1];
+  int total = 0;
+  const int64_t base = pass ? rowptr[row] : 0;
+  for (int eb = e0; eb < e1; eb += 32) {
+    const int e = eb + lane;
+    bool keep = false;
+    int c = 0;
+    if (e < e1) {
+      const int cc = tcol[e];
+      const int l = cc / mz2, k = h + (cc % mz2) - (mz - 1);
+      keep = k >= 0 && k < mz;
+      c = l * mz + k;
+    }
+    const unsigned bal = __ballot_sync(FULL, keep);
+    if (pass && keep) {
+      const int64_t at = base + total + __popc(bal & ((1u << lane) - 1));
+      col[at] = c;
+      if (v32) v32[at] = t32[e];
+      if (v16) v16[at] = t16[e];
+      if (v64) v64[at] = t64[e];
+    }
+    total += __popc(bal);
+  }
+  if (!pass && lane == 0) counts[row] = total;
+}
+
 // Exclusive scan of n int32 counts into out[0..n] (out[n] = total) with a
 // 64-bit running sum; *total receives the exact 64-bit total.  One block.
 __global__ void __launch_bounds__(1024) k_scan(const int32_t* __restrict__ in,
@@ -255,9 +303,11 @@ __global__ void k_round(const double* __restrict__ v64, int64_t n, float* __rest
 // ---- transpose: rows are grouped in blocks of rb consecutive rows ----------
 // cnt[b][c] = entries of block b in column c.
 __global__ void k_block_count(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                              int rb, int cols, int32_t* __restrict__ cnt) {
+                              int rows, int rb, int cols, int32_t* __restrict__ cnt) {
   const int b = blockIdx.x;
-  const int64_t e0 = rowptr[(int64_t)b * rb], e1 = rowptr[(int64_t)(b + 1) * rb];
+  const int ra = b * rb, rz = min(rows, ra + rb);
+  if (ra >= rz) return;
+  const int64_t e0 = rowptr[ra], e1 = rowptr[rz];
   int32_t* c = cnt + (int64_t)b * cols;
   for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(&c[col[e]], 1);
 }
@@ -279,16 +329,19 @@ __global__ void k_col_prefix(int32_t* __restrict__ cnt, int nblocks, int cols,
 
 // Scatter block b's rows in row order: each row's columns are distinct, so a
 // row's entries are written concurrently; rows follow each other after a
-// barrier.  Output rows come out sorted by source row, values copied bitwise.
+// barrier.  Output rows come out sorted by source row; values and payloads
+// are copied bitwise.
 __global__ void k_block_fill(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                              const float* __restrict__ v32, const uint16_t* __restrict__ v16,
-                             const double* __restrict__ v64, int rb, int cols,
-                             const int32_t* __restrict__ tptr, int32_t* __restrict__ cur,
-                             int32_t* __restrict__ tcol, float* __restrict__ t32,
-                             uint16_t* __restrict__ t16, double* __restrict__ t64) {
+                             const double* __restrict__ v64, const int32_t* __restrict__ pay,
+                             int rows, int rb, int cols, const int32_t* __restrict__ tptr,
+                             int32_t* __restrict__ cur, int32_t* __restrict__ tcol,
+                             float* __restrict__ t32, uint16_t* __restrict__ t16,
+                             double* __restrict__ t64, int32_t* __restrict__ tpay) {
   const int b = blockIdx.x;
   int32_t* c = cur + (int64_t)b * cols;
-  for (int r = b * rb; r < (b + 1) * rb; ++r) {
+  const int rz = min(rows, (b + 1) * rb);
+  for (int r = b * rb; r < rz; ++r) {
     const int32_t e0 = rowptr[r], e1 = rowptr[r + 1];
     for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const int32_t k = col[e];
@@ -298,41 +351,16 @@ __global__ void k_block_fill(const int32_t* __restrict__ rowptr, const int32_t* 
       if (t32) t32[pos] = v32[e];
       if (t16) t16[pos] = v16[e];
       if (t64) t64[pos] = v64[e];
+      if (tpay) tpay[pos] = pay[e];
     }
     __syncthreads();
   }
 }
 
-template <class T>
-int dmalloc(T** p, int64_t n, int64_t* bytes) {
-  *p = nullptr;
-  if (n <= 0) n = 1;
-  cudaError_t e = cudaMalloc((void**)p, (size_t)n * sizeof(T));
-  if (e == cudaErrorMemoryAllocation) {
-    cudaGetLastError();
-    return SRT_ERR_OOM;
-  }
-  if (e != cudaSuccess) return SRT_ERR_CUDA;
-  if (bytes) *bytes += n * (int64_t)sizeof(T);
-  return SRT_OK;
-}
+}  // namespace
 
-struct Tmp {  // device temporaries freed on every exit path
-  void* p[8] = {};
-  int n = 0;
-  ~Tmp() {
-    for (int i = 0; i < n; ++i) cudaFree(p[i]);
-  }
-  template <class T>
-  int get(T** out, int64_t count) {
-    int s = dmalloc(out, count, nullptr);
-    if (s == SRT_OK) p[n++] = *out;
-    return s;
-  }
-};
-
-int scan_counts(const int32_t* counts, int32_t* out, int64_t n, long long* dtotal, int64_t* total,
-                cudaStream_t st) {
+int srt_scan_counts(const int32_t* counts, int32_t* out, int64_t n, long long* dtotal,
+                    int64_t* total, cudaStream_t st) {
   k_scan<<<1, 1024, 0, st>>>(counts, out, n, dtotal);
   SRT_CUDA_TRY(cudaGetLastError());
   long long t = 0;
@@ -342,16 +370,45 @@ int scan_counts(const int32_t* counts, int32_t* out, int64_t n, long long* dtota
   return SRT_OK;
 }
 
+int srt_csr_transpose(int rows, int cols, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                      const float* v32, const uint16_t* v16, const double* v64,
+                      const int32_t* pay, int32_t* trowptr, int32_t* tcol, float* t32,
+                      uint16_t* t16, double* t64, int32_t* tpay, cudaStream_t st) {
+  const int nb = rows < 256 ? (rows > 0 ? rows : 1) : 256;
+  const int rb = (rows + nb - 1) / nb;
+  SrtTmp tmp;
+  int32_t *cnt, *tot;
+  long long* dtot;
+  SRT_TRY(tmp.get(&cnt, (int64_t)nb * cols));
+  SRT_TRY(tmp.get(&tot, cols));
+  SRT_TRY(tmp.get(&dtot, 1));
+  SRT_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)nb * cols * sizeof(int32_t), st));
+  k_block_count<<<nb, 512, 0, st>>>(rowptr, col, rows, rb, cols, cnt);
+  SRT_CUDA_TRY(cudaGetLastError());
+  k_col_prefix<<<(cols + 255) / 256, 256, 0, st>>>(cnt, nb, cols, tot);
+  SRT_CUDA_TRY(cudaGetLastError());
+  int64_t got = 0;
+  SRT_TRY(srt_scan_counts(tot, trowptr, cols, dtot, &got, st));
+  if (got != nnz) return SRT_ERR_CUDA;
+  k_block_fill<<<nb, 512, 0, st>>>(rowptr, col, v32, v16, v64, pay, rows, rb, cols, trowptr, cnt,
+                                   tcol, t32, t16, t64, tpay);
+  SRT_CUDA_TRY(cudaGetLastError());
+  SRT_CUDA_TRY(cudaStreamSynchronize(st));
+  return SRT_OK;
+}
+
+namespace {
+
 // Assemble one operator (A1 if a1, else A2) into m, FP64 lengths rounded to
 // the plan's type; the FP64 lengths stay in m->v64 for the caller to keep or free.
 template <bool A1>
-int assemble_one(const GeomDev& G, int wdt, SrtCsr* m, int64_t* dropped,
-                 int64_t* bytes, cudaStream_t st) {
+int assemble_one(const GeomDev& G, int wdt, SrtCsr* m, int64_t* dropped, int64_t* bytes,
+                 cudaStream_t st) {
   const int rows = A1 ? G.n_phi * G.n_ell : G.n_zs * G.n_ell;
   const int cols = A1 ? G.ms * G.ms : G.n_ell * G.mz;
   m->rows = rows;
   m->cols = cols;
-  Tmp tmp;
+  SrtTmp tmp;
   int32_t* counts;
   long long* dtot;
   unsigned long long* ddrop;
@@ -359,64 +416,45 @@ int assemble_one(const GeomDev& G, int wdt, SrtCsr* m, int64_t* dropped,
   SRT_TRY(tmp.get(&dtot, 1));
   SRT_TRY(tmp.get(&ddrop, 1));
   SRT_CUDA_TRY(cudaMemsetAsync(ddrop, 0, sizeof(unsigned long long), st));
-  SRT_TRY(dmalloc(&m->rowptr, (int64_t)rows + 1, bytes));
+  SRT_TRY(srt_dmalloc(&m->rowptr, (int64_t)rows + 1, bytes));
   const int threads = 256;
   const int blocks = (int)(((int64_t)rows * 32 + threads - 1) / threads);
   k_assemble<A1><<<blocks, threads, 0, st>>>(G, rows, 0, counts, nullptr, nullptr, nullptr, ddrop);
   SRT_CUDA_TRY(cudaGetLastError());
   int64_t nnz = 0;
-  SRT_TRY(scan_counts(counts, m->rowptr, rows, dtot, &nnz, st));
+  SRT_TRY(srt_scan_counts(counts, m->rowptr, rows, dtot, &nnz, st));
   if (nnz >= ((int64_t)1 << 31)) return SRT_ERR_GEOMETRY;
   m->nnz = nnz;
   unsigned long long dr = 0;
   SRT_CUDA_TRY(cudaMemcpyAsync(&dr, ddrop, sizeof(dr), cudaMemcpyDeviceToHost, st));
-  double* v64;
-  SRT_TRY(dmalloc(&m->col, nnz, bytes));
-  SRT_TRY(dmalloc(&v64, nnz, nullptr));
-  m->v64 = v64;  // owned by m until released below
-  k_assemble<A1><<<blocks, threads, 0, st>>>(G, rows, 1, nullptr, m->rowptr, m->col, v64, nullptr);
+  SRT_TRY(srt_dmalloc(&m->col, nnz, bytes));
+  SRT_TRY(srt_dmalloc(&m->v64, nnz, nullptr));
+  k_assemble<A1><<<blocks, threads, 0, st>>>(G, rows, 1, nullptr, m->rowptr, m->col, m->v64,
+                                             nullptr);
   SRT_CUDA_TRY(cudaGetLastError());
   if (wdt == SRT_BF16)
-    SRT_TRY(dmalloc(&m->v16, nnz, bytes));
+    SRT_TRY(srt_dmalloc(&m->v16, nnz, bytes));
   else
-    SRT_TRY(dmalloc(&m->v32, nnz, bytes));
-  k_round<<<1216, 256, 0, st>>>(v64, nnz, m->v32, m->v16);
+    SRT_TRY(srt_dmalloc(&m->v32, nnz, bytes));
+  k_round<<<1216, 256, 0, st>>>(m->v64, nnz, m->v32, m->v16);
   SRT_CUDA_TRY(cudaGetLastError());
   SRT_CUDA_TRY(cudaStreamSynchronize(st));
   *dropped = (int64_t)dr;
   return SRT_OK;
 }
 
-// t = transpose of a (rows grouped in blocks of rb for deterministic order).
-int transpose_csr(const SrtCsr& a, int rb, SrtCsr* t, int64_t* bytes, cudaStream_t st) {
+// t = transpose of a: rows sorted by source row, values bit-identical.
+int transpose_csr(const SrtCsr& a, SrtCsr* t, int64_t* bytes, cudaStream_t st) {
   t->rows = a.cols;
   t->cols = a.rows;
   t->nnz = a.nnz;
-  const int nb = a.rows / rb;
-  Tmp tmp;
-  int32_t *cnt, *tot;
-  long long* dtot;
-  SRT_TRY(tmp.get(&cnt, (int64_t)nb * a.cols));
-  SRT_TRY(tmp.get(&tot, a.cols));
-  SRT_TRY(tmp.get(&dtot, 1));
-  SRT_CUDA_TRY(cudaMemsetAsync(cnt, 0, (size_t)nb * a.cols * sizeof(int32_t), st));
-  k_block_count<<<nb, 512, 0, st>>>(a.rowptr, a.col, rb, a.cols, cnt);
-  SRT_CUDA_TRY(cudaGetLastError());
-  k_col_prefix<<<(a.cols + 255) / 256, 256, 0, st>>>(cnt, nb, a.cols, tot);
-  SRT_CUDA_TRY(cudaGetLastError());
-  SRT_TRY(dmalloc(&t->rowptr, (int64_t)a.cols + 1, bytes));
-  int64_t nnz = 0;
-  SRT_TRY(scan_counts(tot, t->rowptr, a.cols, dtot, &nnz, st));
-  if (nnz != a.nnz) return SRT_ERR_CUDA;
-  SRT_TRY(dmalloc(&t->col, nnz, bytes));
-  if (a.v32) SRT_TRY(dmalloc(&t->v32, nnz, bytes));
-  if (a.v16) SRT_TRY(dmalloc(&t->v16, nnz, bytes));
-  if (a.v64) SRT_TRY(dmalloc(&t->v64, nnz, bytes));
-  k_block_fill<<<nb, 512, 0, st>>>(a.rowptr, a.col, a.v32, a.v16, a.v64, rb, a.cols, t->rowptr,
-                                   cnt, t->col, t->v32, t->v16, t->v64);
-  SRT_CUDA_TRY(cudaGetLastError());
-  SRT_CUDA_TRY(cudaStreamSynchronize(st));
-  return SRT_OK;
+  SRT_TRY(srt_dmalloc(&t->rowptr, (int64_t)a.cols + 1, bytes));
+  SRT_TRY(srt_dmalloc(&t->col, a.nnz, bytes));
+  if (a.v32) SRT_TRY(srt_dmalloc(&t->v32, a.nnz, bytes));
+  if (a.v16) SRT_TRY(srt_dmalloc(&t->v16, a.nnz, bytes));
+  if (a.v64) SRT_TRY(srt_dmalloc(&t->v64, a.nnz, bytes));
+  return srt_csr_transpose(a.rows, a.cols, a.nnz, a.rowptr, a.col, a.v32, a.v16, a.v64, nullptr,
+                           t->rowptr, t->col, t->v32, t->v16, t->v64, nullptr, st);
 }
 
 }  // namespace
@@ -430,12 +468,70 @@ void srt_csr_free(SrtCsr* m) {
   *m = SrtCsr();
 }
 
+// The rings coincide with the slab centres: n_zs = mz and the ring range is
+// the volume height (to rounding).
+static bool toeplitz_applies(const srt_geometry& g) {
+  const double h = g.mz * g.dz;
+  return g.n_zs == g.mz && fabs(g.zs_lo + 0.5 * h) <= 1e-12 * h &&
+         fabs(g.zs_hi - 0.5 * h) <= 1e-12 * h && !(g.flags & SRT_CSR_ONLY) &&
+         (g.flags & SRT_TOEPLITZ);
+}
+
+static int expand_toeplitz(const SrtCsr& T, const srt_geometry& g, SrtCsr* a2, int64_t* bytes,
+                           cudaStream_t st) {
+  const int rows = g.n_zs * g.n_ell;
+  a2->rows = rows;
+  a2->cols = g.n_ell * g.mz;
+  SrtTmp tmp;
+  int32_t* counts;
+  long long* dtot;
+  SRT_TRY(tmp.get(&counts, rows));
+  SRT_TRY(tmp.get(&dtot, 1));
+  SRT_TRY(srt_dmalloc(&a2->rowptr, (int64_t)rows + 1, bytes));
+  const int blocks = (int)(((int64_t)rows * 32 + 255) / 256);
+  k_expand_toeplitz<<<blocks, 256, 0, st>>>(g.mz, g.n_ell, rows, 0, T.rowptr, T.col, T.v32, T.v16,
+                                            T.v64, counts, nullptr, nullptr, nullptr, nullptr,
+                                            nullptr);
+  SRT_CUDA_TRY(cudaGetLastError());
+  int64_t nnz = 0;
+  SRT_TRY(srt_scan_counts(counts, a2->rowptr, rows, dtot, &nnz, st));
+  if (nnz >= ((int64_t)1 << 31)) return SRT_ERR_GEOMETRY;
+  a2->nnz = nnz;
+  SRT_TRY(srt_dmalloc(&a2->col, nnz, bytes));
+  if (T.v32) SRT_TRY(srt_dmalloc(&a2->v32, nnz, bytes));
+  if (T.v16) SRT_TRY(srt_dmalloc(&a2->v16, nnz, bytes));
+  SRT_TRY(srt_dmalloc(&a2->v64, nnz, nullptr));
+  k_expand_toeplitz<<<blocks, 256, 0, st>>>(g.mz, g.n_ell, rows, 1, T.rowptr, T.col, T.v32, T.v16,
+                                            T.v64, nullptr, a2->rowptr, a2->col, a2->v32, a2->v16,
+                                            a2->v64);
+  SRT_CUDA_TRY(cudaGetLastError());
+  SRT_CUDA_TRY(cudaStreamSynchronize(st));
+  return SRT_OK;
+}
+
 int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
   const GeomDev G = make_geom(plan->g);
   const bool keep = (plan->g.flags & SRT_KEEP_F64) != 0;
   const int wdt = plan->g.weight_dtype;
   SRT_TRY(assemble_one<true>(G, wdt, &plan->a1, &plan->dropped1, &plan->bytes, st));
-  SRT_TRY(assemble_one<false>(G, wdt, &plan->a2, &plan->dropped2, &plan->bytes, st));
+  if (toeplitz_applies(plan->g)) {
+    // master tensor: one ring at z = 0 over 2 mz - 1 slabs centred on it
+    GeomDev GT = G;
+    GT.mz = 2 * G.mz - 1;
+    GT.n_zs = 1;
+    GT.zs_lo = -0.5 * G.dz;
+    GT.zs_hi = 0.5 * G.dz;
+    GT.hz = 0.5 * GT.mz * GT.dz;
+    SrtCsr T;
+    int s = assemble_one<false>(GT, wdt, &T, &plan->dropped2, nullptr, st);
+    if (s == SRT_OK) s = expand_toeplitz(T, plan->g, &plan->a2, &plan->bytes, st);
+    if (s == SRT_OK) s = srt_build_toeplitz(plan, T, &plan->bytes);
+    srt_csr_free(&T);
+    SRT_TRY(s);
+    plan->toeplitz = 1;
+  } else {
+    SRT_TRY(assemble_one<false>(G, wdt, &plan->a2, &plan->dropped2, &plan->bytes, st));
+  }
   if (!keep) {  // FP64 lengths are only needed for export: drop before transposing
     cudaFree(plan->a1.v64);
     cudaFree(plan->a2.v64);
@@ -443,7 +539,7 @@ int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
   } else {
     plan->bytes += (plan->a1.nnz + plan->a2.nnz) * (int64_t)sizeof(double);
   }
-  SRT_TRY(transpose_csr(plan->a1, G.n_ell, &plan->a1t, &plan->bytes, st));
-  SRT_TRY(transpose_csr(plan->a2, G.n_ell, &plan->a2t, &plan->bytes, st));
+  SRT_TRY(transpose_csr(plan->a1, &plan->a1t, &plan->bytes, st));
+  SRT_TRY(transpose_csr(plan->a2, &plan->a2t, &plan->bytes, st));
   return SRT_OK;
 }

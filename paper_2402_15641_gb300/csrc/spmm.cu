@@ -157,6 +157,7 @@ int launch(const SrtCsr& A, const V* val, const float* x, int64_t ldx, int64_t b
   return SRT_OK;
 }
 
+
 }  // namespace
 
 int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx, float* y,
@@ -164,3 +165,4 @@ int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx,
   if (wdt == SRT_BF16) return launch<uint16_t>(A, A.v16, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
   return launch<float>(A, A.v32, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
 }
+

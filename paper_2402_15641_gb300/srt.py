@@ -39,6 +39,8 @@ class Geometry:
     ell_hi: float
     weight_dtype: str = "fp32"  # "fp32" | "bf16"
     keep_f64: bool = False
+    csr_only: bool = False
+    toeplitz: bool = False
 
     @staticmethod
     def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, weight_dtype="fp32",
@@ -63,7 +65,9 @@ class Geometry:
         return L.SrtGeometry(self.ms, self.mz, self.dxy, self.dz, self.radius, self.n_phi,
                              self.phi0, self.n_zs, self.zs_lo, self.zs_hi, self.n_ell,
                              self.ell_lo, self.ell_hi, wd,
-                             L.SRT_KEEP_F64 if self.keep_f64 else 0)
+                             (L.SRT_KEEP_F64 if self.keep_f64 else 0)
+                             | (L.SRT_CSR_ONLY if self.csr_only else 0)
+                             | (L.SRT_TOEPLITZ if self.toeplitz else 0))
 
     @property
     def f_shape(self):

@@ -72,10 +72,11 @@ def srt256_inputs():
     return I.crop_phantom("srt256", 64), I.probe("srt256")
 
 
-@pytest.mark.parametrize("wdt,tol", [("fp32", 1e-5), ("bf16", 5e-3)])
-def test_srt256_crop_sampled(srt, orc, srt256_inputs, wdt, tol):
+@pytest.mark.parametrize("wdt,tol,toep", [("fp32", 1e-5, False), ("bf16", 5e-3, False),
+                                          ("fp32", 1e-5, True)])
+def test_srt256_crop_sampled(srt, orc, srt256_inputs, wdt, tol, toep):
     sz = dict(I.sizes("srt256"))
-    g, o = geom_pair(orc, weight_dtype=wdt, **sz)
+    g, o = geom_pair(orc, weight_dtype=wdt, toeplitz=toep, **sz)
     plan = srt.Plan(g)
     f, y = srt256_inputs
     sh, vx = _samples(g, 4096, 96, 41, crop=64)

@@ -212,6 +212,12 @@ def test_adjoint_identity_and_voxel_route(orc):
                        for m in range(g.n_ell)])[::7]
     got = orc.forward_shells(g, f, sel_sh)
     assert np.array_equal(got, af[sel_sh[:, 0], sel_sh[:, 1], sel_sh[:, 2]])
+    # adjoint over a shell subset = full adjoint of data masked to that subset
+    y_mask = np.zeros_like(y)
+    y_mask[sel_sh[:, 0], sel_sh[:, 1], sel_sh[:, 2]] = y[sel_sh[:, 0], sel_sh[:, 1], sel_sh[:, 2]]
+    sub = orc.adjoint_shells(g, sel_sh, y[sel_sh[:, 0], sel_sh[:, 1], sel_sh[:, 2]], nthreads=3)
+    np.testing.assert_allclose(sub, orc.adjoint(g, y_mask), rtol=0,
+                               atol=1e-12 * np.max(np.abs(sub)))
 
 
 # ------------------------------------------------------------- symmetries
