@@ -154,6 +154,29 @@ int srt_adjoint_host(srt_plan_t plan, const float* p_host, float* f_host, int32_
                      void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Forward transform that allocates nothing, for callers that cannot hand the
+ * library a device workspace: programs whose device memory is owned by another
+ * allocator that forbids direct cudaMalloc/cudaFree, code running in callbacks
+ * or plug-ins that may not allocate, and latency-critical loops that cannot
+ * afford an allocation.  (The paper has no counterpart; this is an interface
+ * convenience.)  Same inputs, output and layouts as srt_forward; instead of a
+ * caller workspace it uses a scratch array of SRT_NOALLOC_WORKSPACE_BYTES that
+ * the library keeps in device memory on every GPU that loads it, until the
+ * process exits.
+ *   - Returns SRT_ERR_WORKSPACE when srt_workspace_bytes(plan, batch) exceeds
+ *     SRT_NOALLOC_WORKSPACE_BYTES (use srt_forward then), SRT_ERR_ARG when the
+ *     plan was made on a different device than the current one.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (a runtime call, cudaGetSymbolAddress); make that first call before any
+ *     stream capture begins.
+ *   - All calls on a device share the scratch, which keeps the last call's
+ *     contents (no element needs to start at zero).  Calls whose work overlaps
+ *     on the GPU race on it: order them on one stream.
+ */
+#define SRT_NOALLOC_WORKSPACE_BYTES (32u << 20)
+int srt_forward_noalloc(srt_plan_t plan, const float* f, float* p, int32_t batch, void* stream);
+
+/*
  * FP64 inner product on the device: *out = sum_i (double)a[i] * (double)b[i],
  * summed in a fixed order (deterministic).  a, b: device float[n]; out:
  * device double[1]; workspace: device, >= srt_dot_workspace_bytes() bytes.

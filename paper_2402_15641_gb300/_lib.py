@@ -17,6 +17,7 @@ SRT_FP32, SRT_BF16 = 0, 1
 SRT_KEEP_F64 = 1
 SRT_CSR_ONLY = 2
 SRT_TOEPLITZ = 4
+SRT_NOALLOC_WORKSPACE_BYTES = 32 << 20
 
 
 class SrtGeometry(ctypes.Structure):
@@ -53,6 +54,7 @@ SIGNATURES = {
     "srt_adjoint": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _SZ, _VP]),
     "srt_host_workspace_bytes": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_SZ)]),
     "srt_forward_host": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _SZ, _VP]),
+    "srt_forward_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP]),
     "srt_adjoint_host": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _SZ, _VP]),
     "srt_dot_workspace_bytes": (_SZ, []),
     "srt_dot_f64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _SZ, _VP]),
