@@ -1,0 +1,429 @@
+"""Continuous-batching request server for SRT forward and adjoint solves.
+
+Requests arrive with a geometry, a direction (forward A f or adjoint A^T p)
+and a host payload.  The server:
+  * keeps one Plan per geometry resident on the GPU (built on first use) and
+    admits work by an HBM budget covering plans and execution buffers,
+    evicting idle executors and plans least-recently-used first;
+  * queues requests per (geometry, direction) and turns each queue into one
+    batched transform: B same-plan volumes share one pass over the sparse
+    operators (the batched products of the library), B padded to a power of
+    two <= max_batch so each (plan, direction, B) has one reusable executor;
+  * runs each executor's transform as a captured CUDA graph on one of several
+    streams, so batches of different geometries overlap on the device, while
+    new arrivals are admitted as slots and memory free up (continuous
+    batching, not a queue drained one request at a time);
+  * completes batches by polling CUDA events from the host with a deadline
+    (no device-side waits), and reports p50/p99 latency and throughput.
+
+Every transform runs in the library's CUDA kernels; this module only moves
+payloads, schedules and keeps time.
+"""
+from __future__ import annotations
+
+import collections
+import heapq
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from .srt import Geometry, Plan
+
+FWD, ADJ = "fwd", "adj"
+
+
+@dataclass
+class Request:
+    rid: int
+    key: str
+    direction: str
+    payload: torch.Tensor          # host float32, f_shape (fwd) or p_shape (adj)
+    t_arrival: float = 0.0
+    t_done: float | None = None
+    result: torch.Tensor | None = None
+    error: str | None = None
+    cancelled: bool = False
+    batch: int = 0
+
+    @property
+    def latency(self):
+        return None if self.t_done is None else self.t_done - self.t_arrival
+
+
+class Executor:
+    """Buffers (and a CUDA graph) for one (plan, direction, batch) shape."""
+
+    def __init__(self, plan: Plan, direction: str, batch: int, use_graph: bool):
+        g = plan.geom
+        self.plan, self.direction, self.batch = plan, direction, batch
+        ishape = g.f_shape if direction == FWD else g.p_shape
+        oshape = g.p_shape if direction == FWD else g.f_shape
+        dev = plan.device
+        self.d_in = torch.zeros((batch, *ishape), dtype=torch.float32, device=dev)
+        self.d_out = torch.zeros((batch, *oshape), dtype=torch.float32, device=dev)
+        self.h_in = torch.zeros((batch, *ishape), dtype=torch.float32).pin_memory()
+        self.h_out = torch.zeros((batch, *oshape), dtype=torch.float32).pin_memory()
+        self.ws = torch.empty(plan.workspace_bytes(batch), dtype=torch.uint8, device=dev)
+        self.bytes = (self.d_in.numel() + self.d_out.numel()) * 4 + self.ws.numel()
+        self.graph = None
+        self.busy = False
+        self.last_used = 0.0
+        if use_graph:
+            s = torch.cuda.Stream(device=dev)
+            with torch.cuda.stream(s):
+                self._launch(s)          # warm-up outside capture
+            s.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=s):
+                self._launch(torch.cuda.current_stream())
+
+    def _launch(self, stream):
+        if self.direction == FWD:
+            self.plan.forward(self.d_in, out=self.d_out, workspace=self.ws, stream=stream)
+        else:
+            self.plan.adjoint(self.d_in, out=self.d_out, workspace=self.ws, stream=stream)
+
+    def run(self, stream):
+        """Enqueue H2D copy, transform (graph replay) and D2H copy on stream."""
+        with torch.cuda.stream(stream):
+            self.d_in.copy_(self.h_in, non_blocking=True)
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._launch(stream)
+            self.h_out.copy_(self.d_out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return ev
+
+
+@dataclass
+class _InFlight:
+    ex: Executor
+    reqs: list
+    event: object
+    slot: int
+    deadline: float
+
+
+@dataclass
+class ServerStats:
+    completed: int = 0
+    failed: int = 0
+    cancelled: int = 0
+    batches: int = 0
+    batch_hist: collections.Counter = field(default_factory=collections.Counter)
+    plan_builds: int = 0
+    evictions: int = 0
+    deferred: int = 0
+
+
+class Server:
+    def __init__(self, geometries: dict, budget_bytes: int, max_batch: int = 16, n_streams: int = 4,
+                 use_graphs: bool = True, batching: bool = True, deadline_s: float = 30.0,
+                 plan_factory=Plan, clock=time.perf_counter):
+        self.geoms = dict(geometries)
+        self.budget = int(budget_bytes)
+        self.max_batch = max(1, int(max_batch)) if batching else 1
+        self.use_graphs = use_graphs
+        self.deadline_s = deadline_s
+        self.plan_factory = plan_factory
+        self.clock = clock
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.free_slots = list(range(n_streams))
+        self.plans: dict = {}
+        self.plan_used: dict = {}
+        self.bad_keys: dict = {}
+        self.executors: dict = {}      # (key, dir, B) -> [Executor]
+        self.queues: dict = collections.OrderedDict()
+        self.inflight: list = []
+        self.done: list = []
+        self.stats = ServerStats()
+        self._ids = 0
+
+    # ------------------------------------------------------------ memory
+    def used_bytes(self):
+        b = sum(p.info["device_bytes"] for p in self.plans.values())
+        b += sum(e.bytes for lst in self.executors.values() for e in lst)
+        return b
+
+    def _evict(self, need: int, protect: str | None) -> bool:
+        """Free idle executors, then idle plans, LRU first, until need fits."""
+        while self.used_bytes() + need > self.budget:
+            idle = [(e.last_used, k, e) for k, lst in self.executors.items() for e in lst
+                    if not e.busy]
+            if idle:
+                _, k, e = min(idle, key=lambda t: t[0])
+                self.executors[k].remove(e)
+                if not self.executors[k]:
+                    del self.executors[k]
+                self.stats.evictions += 1
+                continue
+            busy_keys = {k[0] for k, lst in self.executors.items() for e in lst if e.busy}
+            queued = {k[0] for k, q in self.queues.items() if q}
+            idle_plans = [(self.plan_used[k], k) for k in self.plans
+                          if k != protect and k not in busy_keys and k not in queued]
+            if not idle_plans:
+                return False
+            _, k = min(idle_plans)
+            self.plans.pop(k).close()
+            self.stats.evictions += 1
+        return True
+
+    def _plan(self, key):
+        if key in self.plans:
+            self.plan_used[key] = self.clock()
+            return self.plans[key]
+        geom = self.geoms[key]
+        plan = self.plan_factory(geom)
+        self.stats.plan_builds += 1
+        self.plans[key] = plan
+        self.plan_used[key] = self.clock()
+        if self.used_bytes() > self.budget and not self._evict(0, protect=key):
+            self.plans.pop(key).close()
+            raise MemoryError(f"plan {key} exceeds the HBM budget")
+        return plan
+
+    def _executor(self, key, direction, B):
+        for e in self.executors.get((key, direction, B), []):
+            if not e.busy:
+                return e
+        plan = self.plans[key]
+        g = plan.geom
+        ni = int(np.prod(g.f_shape if direction == FWD else g.p_shape))
+        no = int(np.prod(g.p_shape if direction == FWD else g.f_shape))
+        need = B * (ni + no) * 4 + plan.workspace_bytes(B)
+        if not self._evict(need, protect=key):
+            return None
+        e = Executor(plan, direction, B, self.use_graphs)
+        self.executors.setdefault((key, direction, B), []).append(e)
+        return e
+
+    # ------------------------------------------------------------ requests
+    def submit(self, key: str, direction: str, payload: torch.Tensor, t_arrival=None) -> Request:
+        self._ids += 1
+        r = Request(self._ids, key, direction, payload,
+                    self.clock() if t_arrival is None else t_arrival)
+        if key not in self.geoms or direction not in (FWD, ADJ):
+            return self._fail(r, "unknown geometry or direction")
+        if key in self.bad_keys:
+            return self._fail(r, self.bad_keys[key])
+        g = self.geoms[key]
+        shape = tuple(g.f_shape if direction == FWD else g.p_shape)
+        if tuple(payload.shape) != shape or payload.dtype != torch.float32:
+            return self._fail(r, f"payload must be float32 {shape}")
+        self.queues.setdefault((key, direction), collections.deque()).append(r)
+        return r
+
+    def cancel(self, r: Request):
+        r.cancelled = True
+        q = self.queues.get((r.key, r.direction))
+        if q and r in q:
+            q.remove(r)
+            self.stats.cancelled += 1
+
+    def _fail(self, r, msg):
+        r.error = msg
+        r.t_done = self.clock()
+        self.stats.failed += 1
+        self.done.append(r)
+        return r
+
+    # ------------------------------------------------------------ scheduling
+    def _complete(self):
+        still = []
+        now = self.clock()
+        for f in self.inflight:
+            if f.event.query():
+                for i, r in enumerate(f.reqs):
+                    if r.cancelled:
+                        self.stats.cancelled += 1
+                        continue
+                    r.result = f.ex.h_out[i].clone()
+                    r.t_done = self.clock()
+                    r.batch = len(f.reqs)
+                    self.stats.completed += 1
+                    self.done.append(r)
+                f.ex.busy = False
+                f.ex.last_used = now
+                self.free_slots.append(f.slot)
+            elif now > f.deadline:
+                for r in f.reqs:  # the host stops waiting; buffers stay busy
+                    self._fail(r, "timeout")
+                f.deadline = math.inf
+                still.append(f)
+            else:
+                still.append(f)
+        self.inflight = still
+
+    def _launch_ready(self):
+        for qkey in list(self.queues.keys()):
+            q = self.queues[qkey]
+            if not q or not self.free_slots:
+                continue
+            key, direction = qkey
+            try:
+                self._plan(key)
+            except MemoryError as exc:
+                if not self.inflight and not self.plans:
+                    while q:  # nothing left to evict: it can never fit
+                        self._fail(q.popleft(), str(exc))
+                else:
+                    self.stats.deferred += 1
+                continue
+            except Exception as exc:  # malformed geometry, failed build
+                self.bad_keys[key] = f"plan build failed: {exc}"
+                while q:
+                    self._fail(q.popleft(), self.bad_keys[key])
+                continue
+            n = min(len(q), self.max_batch)
+            B = 1 << (n - 1).bit_length()
+            ex = self._executor(key, direction, B)
+            if ex is None:
+                if not self.inflight:  # nothing will free memory: it can never fit
+                    while q:
+                        self._fail(q.popleft(), f"request for {key} exceeds the HBM budget")
+                else:
+                    self.stats.deferred += 1
+                continue
+            reqs = [q.popleft() for _ in range(n)]
+            for i, r in enumerate(reqs):
+                ex.h_in[i].copy_(r.payload)
+            if n < B:
+                ex.h_in[n:].zero_()
+            slot = self.free_slots.pop()
+            ex.busy = True
+            ev = ex.run(self.streams[slot])
+            self.inflight.append(_InFlight(ex, reqs, ev, slot, self.clock() + self.deadline_s))
+            self.stats.batches += 1
+            self.stats.batch_hist[n] += 1
+            self.queues.move_to_end(qkey)  # round robin between queues
+
+    def step(self):
+        self._complete()
+        self._launch_ready()
+
+    def pending(self):
+        return bool(self.inflight) or any(self.queues.values())
+
+    def drain(self, timeout_s: float = 120.0):
+        t_end = self.clock() + timeout_s
+        while self.pending() and self.clock() < t_end:
+            self.step()
+        if self.pending():
+            raise TimeoutError("server did not drain in time")
+
+    def close(self):
+        torch.cuda.synchronize()
+        self.executors.clear()
+        for p in self.plans.values():
+            p.close()
+        self.plans.clear()
+
+
+# ---------------------------------------------------------------------------
+def latency_summary(reqs):
+    lat = np.array([r.latency for r in reqs if r.latency is not None and r.error is None])
+    if len(lat) == 0:
+        return {"n": 0}
+    return {"n": int(len(lat)), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3)}
+
+
+def serving_geometries(edges=(64, 96, 128, 192), n_phis=(128, 256)) -> dict:
+    """The serving mix: cubes of each edge at 25.6 mm field of view, R = 20 mm,
+    rings = edge, radius bins = 4 * edge, for each number of columns."""
+    from . import inputs as I
+    out = {}
+    for e in edges:
+        for nphi in n_phis:
+            out[f"{e}^3/{nphi}"] = Geometry.from_sizes(I.sizes(I.serving_geometry(e, nphi)))
+    return out
+
+
+def poisson_run(server: Server, rate: float, duration_s: float, payloads: dict, seed: int = 3,
+                max_requests: int | None = None):
+    """Drive the server with Poisson arrivals (rate per second), 50/50 forward
+    and adjoint, geometry uniform over the server's mix; payloads[(key, dir)]
+    is a list of host tensors drawn from round robin.  Returns the requests."""
+    rng = np.random.default_rng(seed)
+    keys = sorted(server.geoms)
+    t0 = server.clock()
+    t_next = t0 + rng.exponential(1.0 / rate)
+    reqs = []
+    counters = collections.Counter()
+    while True:
+        now = server.clock()
+        while t_next <= now and t_next - t0 < duration_s:
+            key = keys[int(rng.integers(len(keys)))]
+            d = FWD if rng.random() < 0.5 else ADJ
+            pool = payloads[(key, d)]
+            pl = pool[counters[(key, d)] % len(pool)]
+            counters[(key, d)] += 1
+            reqs.append(server.submit(key, d, pl, t_arrival=t_next))
+            t_next += rng.exponential(1.0 / rate)
+            if max_requests and len(reqs) >= max_requests:
+                t_next = math.inf
+        server.step()
+        if (t_next - t0 >= duration_s or t_next == math.inf) and not server.pending():
+            break
+    return reqs
+
+
+def make_payloads(geoms: dict, per: int = 2, seed: int = 3) -> dict:
+    """Seeded ball phantoms (forward) and N(0, 1) data (adjoint), pinned."""
+    from . import inputs as I
+    out = {}
+    for i, (key, g) in enumerate(sorted(geoms.items())):
+        rng = np.random.default_rng(seed + 17 * i)
+        fw, ad = [], []
+        for _ in range(per):
+            f, _ = I.balls(g.ms, g.mz, g.dxy, g.dz, 8, rng)
+            fw.append(torch.from_numpy(f.astype(np.float32)).pin_memory())
+            ad.append(torch.from_numpy(rng.standard_normal(g.p_shape).astype(np.float32))
+                      .pin_memory())
+        out[(key, FWD)], out[(key, ADJ)] = fw, ad
+    return out
+
+
+def main(argv=None):
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="SRT serving benchmark (continuous batching)")
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=30.0)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--max-batch", type=int, default=16)
+    ap.add_argument("--streams", type=int, default=4)
+    ap.add_argument("--edges", default="64,96,128,192")
+    ap.add_argument("--baseline", action="store_true", help="also run unbatched, no graphs")
+    a = ap.parse_args(argv)
+    geoms = serving_geometries(tuple(int(x) for x in a.edges.split(",")))
+    payloads = make_payloads(geoms)
+    results = {}
+    modes = [("batched", dict(max_batch=a.max_batch, use_graphs=True, batching=True))]
+    if a.baseline:
+        modes.append(("unbatched_fp32", dict(max_batch=1, use_graphs=False, batching=False)))
+    for name, kw in modes:
+        srv = Server(geoms, int(a.budget_gb * 2**30), n_streams=a.streams, **kw)
+        # build plans up front so latencies measure serving, not plan builds
+        for k in geoms:
+            srv._plan(k)
+        t0 = time.perf_counter()
+        reqs = poisson_run(srv, a.rate, a.duration, payloads)
+        wall = time.perf_counter() - t0
+        ok = [r for r in reqs if r.error is None and not r.cancelled]
+        results[name] = dict(latency_summary(ok), throughput_rps=len(ok) / wall,
+                             requests=len(reqs), failed=srv.stats.failed,
+                             batches=srv.stats.batches,
+                             mean_batch=len(ok) / max(1, srv.stats.batches),
+                             hbm_used_gb=srv.used_bytes() / 2**30)
+        srv.close()
+    print(json.dumps({"rate_per_s": a.rate, "duration_s": a.duration, "modes": results}))
+
+
+if __name__ == "__main__":
+    main()

@@ -43,14 +43,14 @@ class Geometry:
     toeplitz: bool = False
 
     @staticmethod
-    def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, weight_dtype="fp32",
-                keep_f64=False) -> "Geometry":
-        """Default readings, computed by the library (srt_geometry_default)."""
+    def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, **options) -> "Geometry":
+        """Default readings, computed by the library (srt_geometry_default);
+        options set weight_dtype / keep_f64 / csr_only / toeplitz."""
         g = L.SrtGeometry()
         check(L.lib().srt_geometry_default(ctypes.byref(g), ms, mz, dxy, dz, radius, n_phi, n_zs,
                                            n_ell), "srt_geometry_default")
         return Geometry(g.ms, g.mz, g.dxy, g.dz, g.radius, g.n_phi, g.phi0, g.n_zs, g.zs_lo,
-                        g.zs_hi, g.n_ell, g.ell_lo, g.ell_hi, weight_dtype, keep_f64)
+                        g.zs_hi, g.n_ell, g.ell_lo, g.ell_hi, **options)
 
     @staticmethod
     def from_sizes(d: dict, **kw) -> "Geometry":

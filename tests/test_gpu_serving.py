@@ -1,0 +1,125 @@
+"""Serving loop: continuous batching over resident plans with CUDA graphs.
+Each result must equal the same request computed alone; admission honours
+the HBM budget; failures stay on the host (bad geometry, failed plan build,
+budget exhaustion, cancellation)."""
+import numpy as np
+import pytest
+
+from paper_2402_15641_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2402_15641_gb300 import build, serving as SV
+    from paper_2402_15641_gb300.srt import Geometry, Plan
+    assert torch.cuda.is_available()
+    build.build()
+    geoms = {
+        "a": Geometry.from_sizes(I.sizes(I.serving_geometry(16, 32))),
+        "b": Geometry.from_sizes(I.sizes(I.serving_geometry(24, 48))),
+        "c": Geometry.from_sizes(I.sizes(I.serving_geometry(20, 40))),
+    }
+    payloads = SV.make_payloads(geoms, per=3)
+    return SV, Plan, geoms, payloads
+
+
+_ALONE = {}
+
+
+def _alone(Plan, geoms, r):
+    if r.key not in _ALONE:
+        _ALONE[r.key] = Plan(geoms[r.key])
+    plan = _ALONE[r.key]
+    x = r.payload.cuda()
+    out = plan.forward(x) if r.direction == "fwd" else plan.adjoint(x)
+    return out.cpu()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_results_in_the_mix_equal_results_alone(env, graphs):
+    import torch
+    SV, Plan, geoms, payloads = env
+    srv = SV.Server(geoms, budget_bytes=8 << 30, max_batch=16, n_streams=3, use_graphs=graphs)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(60):
+        key = "abc"[int(rng.integers(3))]
+        d = "fwd" if rng.random() < 0.5 else "adj"
+        reqs.append(srv.submit(key, d, payloads[(key, d)][i % 3]))
+        if i % 7 == 0:
+            srv.step()  # arrivals interleaved with completions
+    srv.drain()
+    assert all(r.error is None and r.result is not None for r in reqs)
+    assert max(srv.stats.batch_hist) > 1  # same-plan requests were batched
+    for r in reqs:
+        assert torch.equal(r.result, _alone(Plan, geoms, r)), (r.rid, r.key, r.direction)
+    srv.close()
+
+
+def test_budget_evicts_and_serves_alternating_plans(env):
+    SV, Plan, geoms, payloads = env
+    pa, pb = Plan(geoms["a"]), Plan(geoms["b"])
+    plans = [pa.info["device_bytes"], pb.info["device_bytes"]]
+    execs = [(int(np.prod(geoms[k].f_shape)) + int(np.prod(geoms[k].p_shape))) * 4
+             + p.workspace_bytes(1) for k, p in (("a", pa), ("b", pb))]
+    budget = max(plans) + max(execs) + (64 << 10)  # room for one plan and one executor
+    assert budget < sum(plans) + sum(execs)
+    pa.close(), pb.close()
+    srv = SV.Server({k: geoms[k] for k in "ab"}, budget_bytes=budget, max_batch=1, n_streams=1)
+    reqs = []
+    for i in range(8):
+        key = "ab"[i % 2]
+        reqs.append(srv.submit(key, "fwd", payloads[(key, "fwd")][0]))
+        srv.drain()
+    assert all(r.error is None for r in reqs)
+    assert srv.stats.evictions > 0 and srv.used_bytes() <= budget
+    srv.close()
+
+
+def test_host_side_failures(env):
+    import torch
+    SV, Plan, geoms, payloads = env
+    bad = geoms["a"].with_(radius=0.1)  # sensors inside the volume: rejected by srt_plan
+
+    def factory(g):
+        if g.ms == 24:
+            raise RuntimeError("injected plan-build failure")
+        return Plan(g)
+
+    srv = SV.Server({"a": geoms["a"], "b": geoms["b"], "bad": bad}, budget_bytes=8 << 30,
+                    plan_factory=factory)
+    ok = srv.submit("a", "fwd", payloads[("a", "fwd")][0])
+    r_bad = srv.submit("bad", "fwd", payloads[("a", "fwd")][0])
+    r_inj = srv.submit("b", "adj", payloads[("b", "adj")][0])
+    r_unknown = srv.submit("zzz", "fwd", payloads[("a", "fwd")][0])
+    r_shape = srv.submit("a", "adj", payloads[("a", "fwd")][0])
+    r_cancel = srv.submit("a", "adj", payloads[("a", "adj")][1])
+    srv.cancel(r_cancel)
+    srv.drain()
+    assert ok.error is None and ok.result is not None
+    assert "plan build failed" in r_bad.error
+    assert "injected" in r_inj.error
+    assert r_unknown.error and r_shape.error
+    assert r_cancel.result is None and r_cancel.cancelled
+    assert srv.stats.failed == 4 and srv.stats.cancelled == 1
+    srv.close()
+    tiny = SV.Server({"a": geoms["a"]}, budget_bytes=1 << 20)
+    r = tiny.submit("a", "fwd", payloads[("a", "fwd")][0])
+    tiny.drain()
+    assert r.error and "budget" in r.error
+    tiny.close()
+
+
+def test_poisson_run_reports_latency(env):
+    SV, Plan, geoms, payloads = env
+    srv = SV.Server(geoms, budget_bytes=8 << 30)
+    for k in geoms:
+        srv._plan(k)
+    reqs = SV.poisson_run(srv, rate=400.0, duration_s=1.0, payloads=payloads, seed=3)
+    s = SV.latency_summary(reqs)
+    assert s["n"] == len(reqs) > 100
+    assert 0 < s["p50_ms"] <= s["p99_ms"]
+    srv.close()
