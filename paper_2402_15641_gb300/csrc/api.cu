@@ -78,7 +78,9 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   const int64_t nb = (int64_t)B * g.n_phi;  // dense width of the second stage
   mark(p, 0, 0, st);
   // Y1[b][j][l][k] = A1 F_b (CRT in the first plane, all slabs at once)
-  SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B, st));
+  // rows (j, l) visited radius-chunk-major across sensor columns (L2 reuse of F)
+  SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B, st,
+                   g.n_phi, g.n_ell));
   mark(p, 0, 1, st);
   if (p->toeplitz) {
     // slabs Y1'[l][z][n] in tiles, then the vertical CRT as a z-correlation
@@ -91,7 +93,10 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   } else {
     SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
     mark(p, 0, 2, st);
-    SRT_TRY(srt_spmm(p->a2, g.weight_dtype, w1, nb, 0, w0, nb, 0, (int)nb, 1, st));
+    // rows (h, m) visited radius-chunk-major across rings: blocks running at
+    // the same time gather a narrow band of Y1' rows, which stays in L2
+    SRT_TRY(srt_spmm(p->a2, g.weight_dtype, w1, nb, 0, w0, nb, 0, (int)nb, 1, st, g.n_zs,
+                     g.n_ell));
     mark(p, 0, 3, st);
     SRT_TRY(srt_transpose(w0, nb, g.n_phi, out, r2, (int64_t)g.n_phi * r2, (int)r2, g.n_phi, B, st));
   }
