@@ -94,9 +94,11 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
     SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
     mark(p, 0, 2, st);
     // rows (h, m) visited radius-chunk-major across rings: blocks running at
-    // the same time gather a narrow band of Y1' rows, which stays in L2
+    // the same time gather a narrow band of Y1' rows, which stays in L2.  A
+    // block owns 4 rings x 2 radii: neighbouring rings gather shifted copies
+    // of the same cells (A2 is Toeplitz in z), so its warps share L1 lines.
     SRT_TRY(srt_spmm(p->a2, g.weight_dtype, w1, nb, 0, w0, nb, 0, (int)nb, 1, st, g.n_zs,
-                     g.n_ell));
+                     g.n_ell, 4));
     mark(p, 0, 3, st);
     SRT_TRY(srt_transpose(w0, nb, g.n_phi, out, r2, (int64_t)g.n_phi * r2, (int)r2, g.n_phi, B, st));
   }
@@ -131,7 +133,10 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
     f1 = w0;
   }
   mark(p, 1, 3, st);
-  SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f, g.mz, pix * g.mz, g.mz, B, st));
+  // rows (pixels) in blocks of 4 x 2 pixels: a circle crossing a compact
+  // tile touches more of its pixels than of a line of 8, so warps share L1
+  SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f, g.mz, pix * g.mz, g.mz, B, st,
+                   g.ms, g.ms, 4));
   mark(p, 1, 4, st);
   if (p->timing) p->have_times[1] = 1;
   return SRT_OK;

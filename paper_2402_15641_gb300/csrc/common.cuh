@@ -106,10 +106,11 @@ int srt_tiles_from_cols(const float* in, int nkey, int npos, int ncols, float* o
                         cudaStream_t stream);
 
 // y[b][r][n] = sum_e A[r, col[e]] * x[b][col[e]][n] for n < ncols.  With G > 0
-// the rows (G groups of R) are visited chunk-major across groups.
+// the rows (G groups of R) are visited chunk-major across groups, a block
+// owning TG groups (1, 2, 4 or 8) x 8/TG consecutive rows of each.
 int srt_spmm(const SrtCsr& A, int weight_dtype, const float* x, int64_t ldx, int64_t bsx, float* y,
              int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t stream, int G = 0,
-             int R = 0);
+             int R = 0, int TG = 1);
 
 // out[b*obs + c*old + r] = in[b*ibs + r*ild + c] for r < rows, c < cols.
 int srt_transpose(const float* in, int64_t ild, int64_t ibs, float* out, int64_t old, int64_t obs,

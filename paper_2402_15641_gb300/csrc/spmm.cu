@@ -27,20 +27,22 @@ __device__ __forceinline__ float wval<uint16_t>(uint16_t v) {
 // a warp covers CH chunks.  Requires ncols, ldx, ldy multiples of 4 and
 // 16-byte aligned bases.
 // Block-to-rows order.  Rows come in G groups of R rows (r = g*R + i).  With
-// G > 0, consecutive blocks take the same 8-row chunk of i in consecutive
-// groups (chunk-major): all groups advance through i together, so the dense
-// rows gathered by concurrently running blocks stay within a narrow band of
-// the operand (L2 reuse), while a block's 8 warps keep consecutive i (L1
+// G > 0 a block owns a tile of TG groups x 8/TG consecutive i, and
+// consecutive blocks take the same chunk of i in consecutive group tiles
+// (chunk-major): all groups advance through i together, so the dense rows
+// gathered by concurrently running blocks stay within a narrow band of the
+// operand (L2 reuse), while a block's 8 warps gather overlapping rows (L1
 // reuse).  With G = 0 blocks take consecutive rows.
-__device__ __forceinline__ int block_row(int G, int R) {
+__device__ __forceinline__ int block_row(int G, int R, int TG) {
   const int w = threadIdx.x >> 5;
   if (G <= 0) return blockIdx.x * (blockDim.x >> 5) + w;
-  const int chunks = (R + 7) >> 3;
+  const int TI = 8 / TG;
+  const int chunks = (R + TI - 1) / TI, tiles = (G + TG - 1) / TG;
   const int bid = blockIdx.x;
-  const int c = bid / G, g = bid - c * G;
+  const int c = bid / tiles, t = bid - c * tiles;
   if (c >= chunks) return -1;
-  const int i = c * 8 + w;
-  return i < R ? g * R + i : -1;
+  const int g = t * TG + w / TI, i = c * TI + w % TI;
+  return (g < G && i < R) ? g * R + i : -1;
 }
 
 template <typename V, int CH>
@@ -49,9 +51,9 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int rows, const int32_t* __res
                                                   const V* __restrict__ val,
                                                   const float* __restrict__ x, int64_t ldx,
                                                   int64_t bsx, float* __restrict__ y, int64_t ldy,
-                                                  int64_t bsy, int ncols, int G, int R) {
+                                                  int64_t bsy, int ncols, int G, int R, int TG) {
   const int lane = threadIdx.x & 31;
-  const int row = block_row(G, R);
+  const int row = block_row(G, R, TG);
   if (row < 0 || row >= rows) return;
   x += blockIdx.z * bsx;
   y += blockIdx.z * bsy;
@@ -140,31 +142,33 @@ __global__ void __launch_bounds__(256) k_spmm_scalar(int rows, const int32_t* __
 
 template <typename V>
 int launch(const SrtCsr& A, const V* val, const float* x, int64_t ldx, int64_t bsx, float* y,
-           int64_t ldy, int64_t bsy, int ncols, int batch, int G, int R, cudaStream_t st) {
+           int64_t ldy, int64_t bsy, int ncols, int batch, int G, int R, int TG, cudaStream_t st) {
   const int rows_per_block = 8;
   dim3 block(256);
   const bool vec = (ncols % 4 == 0) && (ldx % 4 == 0) && (ldy % 4 == 0) && (bsx % 4 == 0) &&
                    (bsy % 4 == 0) && ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0);
   if (G > 0 && (int64_t)G * R != A.rows) G = 0;
-  const int gx = G > 0 ? G * ((R + 7) / 8) : (A.rows + rows_per_block - 1) / rows_per_block;
+  if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 1;
+  const int gx = G > 0 ? ((G + TG - 1) / TG) * ((R + 8 / TG - 1) / (8 / TG))
+                       : (A.rows + rows_per_block - 1) / rows_per_block;
   if (vec) {
     const int chunks = (ncols + 127) / 128;
     if (chunks >= 4) {
       dim3 grid(gx, (ncols + 511) / 512, batch);
       k_spmm_vec<V, 4><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                               bsy, ncols, G, R);
+                                               bsy, ncols, G, R, TG);
     } else if (chunks == 3) {
       dim3 grid(gx, 1, batch);
       k_spmm_vec<V, 3><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                               bsy, ncols, G, R);
+                                               bsy, ncols, G, R, TG);
     } else if (chunks == 2) {
       dim3 grid(gx, 1, batch);
       k_spmm_vec<V, 2><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                               bsy, ncols, G, R);
+                                               bsy, ncols, G, R, TG);
     } else {
       dim3 grid(gx, 1, batch);
       k_spmm_vec<V, 1><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                               bsy, ncols, G, R);
+                                               bsy, ncols, G, R, TG);
     }
   } else {
     dim3 grid((A.rows + rows_per_block - 1) / rows_per_block, (ncols + 127) / 128, batch);
@@ -179,9 +183,10 @@ int launch(const SrtCsr& A, const V* val, const float* x, int64_t ldx, int64_t b
 }  // namespace
 
 int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx, float* y,
-             int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t st, int G, int R) {
+             int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t st, int G, int R,
+             int TG) {
   if (wdt == SRT_BF16)
-    return launch<uint16_t>(A, A.v16, x, ldx, bsx, y, ldy, bsy, ncols, batch, G, R, st);
-  return launch<float>(A, A.v32, x, ldx, bsx, y, ldy, bsy, ncols, batch, G, R, st);
+    return launch<uint16_t>(A, A.v16, x, ldx, bsx, y, ldy, bsy, ncols, batch, G, R, TG, st);
+  return launch<float>(A, A.v32, x, ldx, bsx, y, ldy, bsy, ncols, batch, G, R, TG, st);
 }
 

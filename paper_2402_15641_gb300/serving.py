@@ -54,18 +54,20 @@ class Request:
 
 
 class Executor:
-    """Buffers (and a CUDA graph) for one (plan, direction, batch) shape."""
+    """Device buffers (and a CUDA graph) for one (plan, direction, batch) shape.
+    Payloads are copied straight from the requests' host tensors into the
+    batch slots, and results straight into per-request pinned host tensors
+    (torch's caching host allocator recycles them), so the server thread does
+    no host-side copies of its own."""
 
     def __init__(self, plan: Plan, direction: str, batch: int, use_graph: bool):
         g = plan.geom
         self.plan, self.direction, self.batch = plan, direction, batch
         ishape = g.f_shape if direction == FWD else g.p_shape
-        oshape = g.p_shape if direction == FWD else g.f_shape
+        self.oshape = tuple(g.p_shape if direction == FWD else g.f_shape)
         dev = plan.device
         self.d_in = torch.zeros((batch, *ishape), dtype=torch.float32, device=dev)
-        self.d_out = torch.zeros((batch, *oshape), dtype=torch.float32, device=dev)
-        self.h_in = torch.zeros((batch, *ishape), dtype=torch.float32).pin_memory()
-        self.h_out = torch.zeros((batch, *oshape), dtype=torch.float32).pin_memory()
+        self.d_out = torch.zeros((batch, *self.oshape), dtype=torch.float32, device=dev)
         self.ws = torch.empty(plan.workspace_bytes(batch), dtype=torch.uint8, device=dev)
         self.bytes = (self.d_in.numel() + self.d_out.numel()) * 4 + self.ws.numel()
         self.graph = None
@@ -86,18 +88,26 @@ class Executor:
         else:
             self.plan.adjoint(self.d_in, out=self.d_out, workspace=self.ws, stream=stream)
 
-    def run(self, stream):
-        """Enqueue H2D copy, transform (graph replay) and D2H copy on stream."""
+    def run(self, stream, payloads):
+        """Enqueue the H2D copies of the payloads into slots 0..n-1, the
+        transform (graph replay) and the D2H copies of those slots on stream.
+        Slots n..B-1 keep stale inputs: batch columns are independent, and
+        their outputs are not read.  Returns (event, host outputs)."""
+        outs = []
         with torch.cuda.stream(stream):
-            self.d_in.copy_(self.h_in, non_blocking=True)
+            for i, pl in enumerate(payloads):
+                self.d_in[i].copy_(pl, non_blocking=True)
             if self.graph is not None:
                 self.graph.replay()
             else:
                 self._launch(stream)
-            self.h_out.copy_(self.d_out, non_blocking=True)
+            for i in range(len(payloads)):
+                o = torch.empty(self.oshape, dtype=torch.float32, pin_memory=True)
+                o.copy_(self.d_out[i], non_blocking=True)
+                outs.append(o)
             ev = torch.cuda.Event()
             ev.record(stream)
-        return ev
+        return ev, outs
 
 
 @dataclass
@@ -107,6 +117,7 @@ class _InFlight:
     event: object
     slot: int
     deadline: float
+    outs: list
 
 
 @dataclass
@@ -242,7 +253,7 @@ class Server:
                     if r.cancelled:
                         self.stats.cancelled += 1
                         continue
-                    r.result = f.ex.h_out[i].clone()
+                    r.result = f.outs[i]
                     r.t_done = self.clock()
                     r.batch = len(f.reqs)
                     self.stats.completed += 1
@@ -290,14 +301,11 @@ class Server:
                     self.stats.deferred += 1
                 continue
             reqs = [q.popleft() for _ in range(n)]
-            for i, r in enumerate(reqs):
-                ex.h_in[i].copy_(r.payload)
-            if n < B:
-                ex.h_in[n:].zero_()
             slot = self.free_slots.pop()
             ex.busy = True
-            ev = ex.run(self.streams[slot])
-            self.inflight.append(_InFlight(ex, reqs, ev, slot, self.clock() + self.deadline_s))
+            ev, outs = ex.run(self.streams[slot], [r.payload for r in reqs])
+            self.inflight.append(_InFlight(ex, reqs, ev, slot, self.clock() + self.deadline_s,
+                                           outs))
             self.stats.batches += 1
             self.stats.batch_hist[n] += 1
             self.queues.move_to_end(qkey)  # round robin between queues
@@ -345,16 +353,19 @@ def serving_geometries(edges=(64, 96, 128, 192), n_phis=(128, 256)) -> dict:
 
 
 def poisson_run(server: Server, rate: float, duration_s: float, payloads: dict, seed: int = 3,
-                max_requests: int | None = None):
+                max_requests: int | None = None, drop_results: bool = False):
     """Drive the server with Poisson arrivals (rate per second), 50/50 forward
     and adjoint, geometry uniform over the server's mix; payloads[(key, dir)]
-    is a list of host tensors drawn from round robin.  Returns the requests."""
+    is a list of host tensors drawn from round robin.  Returns the requests.
+    drop_results releases each result once it has been delivered (a long run
+    at a high rate would otherwise hold every output in host memory)."""
     rng = np.random.default_rng(seed)
     keys = sorted(server.geoms)
     t0 = server.clock()
     t_next = t0 + rng.exponential(1.0 / rate)
     reqs = []
     counters = collections.Counter()
+    seen = len(server.done)
     while True:
         now = server.clock()
         while t_next <= now and t_next - t0 < duration_s:
@@ -368,6 +379,10 @@ def poisson_run(server: Server, rate: float, duration_s: float, payloads: dict, 
             if max_requests and len(reqs) >= max_requests:
                 t_next = math.inf
         server.step()
+        if drop_results:
+            while seen < len(server.done):
+                server.done[seen].result = None
+                seen += 1
         if (t_next - t0 >= duration_s or t_next == math.inf) and not server.pending():
             break
     return reqs
@@ -393,8 +408,14 @@ def main(argv=None):
     import argparse
     import json
     ap = argparse.ArgumentParser(description="SRT serving benchmark (continuous batching)")
-    ap.add_argument("--rate", type=float, default=200.0)
-    ap.add_argument("--duration", type=float, default=30.0)
+    ap.add_argument("--rates", default="200",
+                    help="comma-separated Poisson arrival rates (requests/s)")
+    ap.add_argument("--duration", type=float, default=30.0,
+                    help="arrival window in seconds at the first rate")
+    ap.add_argument("--max-requests", type=int, default=12000,
+                    help="arrivals per rate at most (bounds the overloaded runs)")
+    ap.add_argument("--warmup-s", type=float, default=5.0,
+                    help="untimed run before each mode (executors, graphs, pinned blocks)")
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--max-batch", type=int, default=16)
     ap.add_argument("--streams", type=int, default=4)
@@ -403,26 +424,42 @@ def main(argv=None):
     a = ap.parse_args(argv)
     geoms = serving_geometries(tuple(int(x) for x in a.edges.split(",")))
     payloads = make_payloads(geoms)
-    results = {}
+    rates = [float(x) for x in a.rates.split(",")]
     modes = [("batched", dict(max_batch=a.max_batch, use_graphs=True, batching=True))]
     if a.baseline:
         modes.append(("unbatched_fp32", dict(max_batch=1, use_graphs=False, batching=False)))
+    out = {"duration_s": a.duration, "max_requests": a.max_requests, "warmup_s": a.warmup_s,
+           "budget_gb": a.budget_gb, "geometries": sorted(geoms), "runs": []}
     for name, kw in modes:
         srv = Server(geoms, int(a.budget_gb * 2**30), n_streams=a.streams, **kw)
-        # build plans up front so latencies measure serving, not plan builds
-        for k in geoms:
+        for k in geoms:  # plans up front: latencies measure serving, not plan builds
             srv._plan(k)
-        t0 = time.perf_counter()
-        reqs = poisson_run(srv, a.rate, a.duration, payloads)
-        wall = time.perf_counter() - t0
-        ok = [r for r in reqs if r.error is None and not r.cancelled]
-        results[name] = dict(latency_summary(ok), throughput_rps=len(ok) / wall,
-                             requests=len(reqs), failed=srv.stats.failed,
-                             batches=srv.stats.batches,
-                             mean_batch=len(ok) / max(1, srv.stats.batches),
-                             hbm_used_gb=srv.used_bytes() / 2**30)
+        poisson_run(srv, rates[-1], a.warmup_s, payloads, seed=99, drop_results=True,
+                    max_requests=min(a.max_requests, 3000))
+        for rate in rates:
+            base = dict(srv.stats.__dict__)
+            base_hist = collections.Counter(srv.stats.batch_hist)
+            t0 = time.perf_counter()
+            reqs = poisson_run(srv, rate, a.duration, payloads, drop_results=True,
+                               max_requests=a.max_requests)
+            wall = time.perf_counter() - t0
+            ok = [r for r in reqs if r.error is None and not r.cancelled]
+            batches = srv.stats.batches - base["batches"]
+            hist = srv.stats.batch_hist - base_hist
+            arrivals = [r.t_arrival for r in reqs]
+            out["runs"].append(dict(
+                mode=name, rate_per_s=rate, requests=len(reqs),
+                arrival_window_s=(max(arrivals) - min(arrivals)) if arrivals else 0.0,
+                wall_s=wall, throughput_rps=len(ok) / wall, **latency_summary(ok),
+                failed=srv.stats.failed - base["failed"], batches=batches,
+                mean_batch=len(ok) / max(1, batches),
+                batch_hist={int(k): int(v) for k, v in sorted(hist.items())},
+                evictions=srv.stats.evictions - base["evictions"],
+                hbm_used_gb=srv.used_bytes() / 2**30))
+            print(json.dumps(out["runs"][-1]), flush=True)
+            srv.done.clear()
         srv.close()
-    print(json.dumps({"rate_per_s": a.rate, "duration_s": a.duration, "modes": results}))
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
