@@ -7,8 +7,12 @@ and a host payload.  The server:
     evicting idle executors and plans least-recently-used first;
   * queues requests per (geometry, direction) and turns each queue into one
     batched transform: B same-plan volumes share one pass over the sparse
-    operators (the batched products of the library), B padded to a power of
-    two <= max_batch so each (plan, direction, B) has one reusable executor;
+    operators (the batched products of the library).  B is a power of two <=
+    max_batch (each (plan, direction, B) has one reusable executor), taken
+    DOWN from the queue length so no batch slot computes padding, and capped
+    so that B times the measured device time per volume of that (plan,
+    direction) stays within batch_budget_s: small transforms batch wide,
+    large ones run alone instead of holding a stream for a long batch;
   * runs each executor's transform as a captured CUDA graph on one of several
     streams, so batches of different geometries overlap on the device, while
     new arrivals are admitted as slots and memory free up (continuous
@@ -92,22 +96,38 @@ class Executor:
         """Enqueue the H2D copies of the payloads into slots 0..n-1, the
         transform (graph replay) and the D2H copies of those slots on stream.
         Slots n..B-1 keep stale inputs: batch columns are independent, and
-        their outputs are not read.  Returns (event, host outputs)."""
+        their outputs are not read.  Returns (event, host outputs, (t0, t1))
+        with timing events around the transform."""
         outs = []
         with torch.cuda.stream(stream):
             for i, pl in enumerate(payloads):
                 self.d_in[i].copy_(pl, non_blocking=True)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
             if self.graph is not None:
                 self.graph.replay()
             else:
                 self._launch(stream)
+            t1.record(stream)
             for i in range(len(payloads)):
                 o = torch.empty(self.oshape, dtype=torch.float32, pin_memory=True)
                 o.copy_(self.d_out[i], non_blocking=True)
                 outs.append(o)
             ev = torch.cuda.Event()
             ev.record(stream)
-        return ev, outs
+        return ev, outs, (t0, t1)
+
+
+def batch_size(queued: int, max_batch: int, per_volume_s, budget_s: float) -> int:
+    """Volumes to take from a queue of `queued`: at most max_batch, at most
+    budget_s / per_volume_s when the device time per volume is known, and a
+    power of two (rounded down, so no batch slot computes padding)."""
+    n = min(queued, max_batch)
+    if per_volume_s is not None and per_volume_s > 0:
+        n = min(n, max(1, int(budget_s / per_volume_s)))
+    n = max(1, n)
+    return 1 << (n.bit_length() - 1)
 
 
 @dataclass
@@ -118,6 +138,7 @@ class _InFlight:
     slot: int
     deadline: float
     outs: list
+    timing: tuple
 
 
 @dataclass
@@ -135,12 +156,15 @@ class ServerStats:
 class Server:
     def __init__(self, geometries: dict, budget_bytes: int, max_batch: int = 16, n_streams: int = 4,
                  use_graphs: bool = True, batching: bool = True, deadline_s: float = 30.0,
+                 batch_budget_s: float = 0.010,
                  plan_factory=Plan, clock=time.perf_counter):
         self.geoms = dict(geometries)
         self.budget = int(budget_bytes)
         self.max_batch = max(1, int(max_batch)) if batching else 1
         self.use_graphs = use_graphs
         self.deadline_s = deadline_s
+        self.batch_budget_s = batch_budget_s
+        self.cost: dict = {}           # (key, dir) -> device seconds per volume (EMA)
         self.plan_factory = plan_factory
         self.clock = clock
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
@@ -249,6 +273,11 @@ class Server:
         now = self.clock()
         for f in self.inflight:
             if f.event.query():
+                t0, t1 = f.timing
+                per = t0.elapsed_time(t1) / 1e3 / f.ex.batch
+                ck = (f.reqs[0].key, f.reqs[0].direction)
+                old = self.cost.get(ck)
+                self.cost[ck] = per if old is None else 0.8 * old + 0.2 * per
                 for i, r in enumerate(f.reqs):
                     if r.cancelled:
                         self.stats.cancelled += 1
@@ -290,8 +319,8 @@ class Server:
                 while q:
                     self._fail(q.popleft(), self.bad_keys[key])
                 continue
-            n = min(len(q), self.max_batch)
-            B = 1 << (n - 1).bit_length()
+            B = batch_size(len(q), self.max_batch, self.cost.get(qkey), self.batch_budget_s)
+            n = B
             ex = self._executor(key, direction, B)
             if ex is None:
                 if not self.inflight:  # nothing will free memory: it can never fit
@@ -303,9 +332,9 @@ class Server:
             reqs = [q.popleft() for _ in range(n)]
             slot = self.free_slots.pop()
             ex.busy = True
-            ev, outs = ex.run(self.streams[slot], [r.payload for r in reqs])
+            ev, outs, timing = ex.run(self.streams[slot], [r.payload for r in reqs])
             self.inflight.append(_InFlight(ex, reqs, ev, slot, self.clock() + self.deadline_s,
-                                           outs))
+                                           outs, timing))
             self.stats.batches += 1
             self.stats.batch_hist[n] += 1
             self.queues.move_to_end(qkey)  # round robin between queues
@@ -404,6 +433,36 @@ def make_payloads(geoms: dict, per: int = 2, seed: int = 3) -> dict:
     return out
 
 
+def probe_costs(geoms: dict, batches=(1, 16), reps: int = 10):
+    """Device milliseconds per volume of each (geometry, direction) at each
+    batch size (CUDA events around reps back-to-back transforms)."""
+    rows = []
+    for key in sorted(geoms):
+        g = geoms[key]
+        plan = Plan(g)
+        for d in (FWD, ADJ):
+            ish, osh = (g.f_shape, g.p_shape) if d == FWD else (g.p_shape, g.f_shape)
+            row = {"geometry": key, "direction": d}
+            for B in batches:
+                x = torch.randn((B, *ish), device=plan.device)
+                y = torch.empty((B, *osh), device=plan.device)
+                ws = plan.workspace(B)
+                run = plan.forward if d == FWD else plan.adjoint
+                run(x, out=y, workspace=ws)
+                torch.cuda.synchronize()
+                t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0.record()
+                for _ in range(reps):
+                    run(x, out=y, workspace=ws)
+                t1.record()
+                t1.synchronize()
+                row[f"ms_per_volume_b{B}"] = t0.elapsed_time(t1) / reps / B
+                del x, y, ws
+            rows.append(row)
+        plan.close()
+    return rows
+
+
 def main(argv=None):
     import argparse
     import json
@@ -418,17 +477,28 @@ def main(argv=None):
                     help="untimed run before each mode (executors, graphs, pinned blocks)")
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--max-batch", type=int, default=16)
+    ap.add_argument("--batch-budget-ms", type=float, default=10.0,
+                    help="device time per batch the batch size is capped to")
     ap.add_argument("--streams", type=int, default=4)
     ap.add_argument("--edges", default="64,96,128,192")
     ap.add_argument("--baseline", action="store_true", help="also run unbatched, no graphs")
+    ap.add_argument("--probe", action="store_true",
+                    help="only print the device time per volume of every geometry and "
+                         "direction at batch 1 and at --max-batch")
     a = ap.parse_args(argv)
     geoms = serving_geometries(tuple(int(x) for x in a.edges.split(",")))
+    if a.probe:
+        for row in probe_costs(geoms, (1, a.max_batch)):
+            print(json.dumps(row), flush=True)
+        return
     payloads = make_payloads(geoms)
     rates = [float(x) for x in a.rates.split(",")]
-    modes = [("batched", dict(max_batch=a.max_batch, use_graphs=True, batching=True))]
+    modes = [("batched", dict(max_batch=a.max_batch, use_graphs=True, batching=True,
+                              batch_budget_s=a.batch_budget_ms / 1e3))]
     if a.baseline:
         modes.append(("unbatched_fp32", dict(max_batch=1, use_graphs=False, batching=False)))
     out = {"duration_s": a.duration, "max_requests": a.max_requests, "warmup_s": a.warmup_s,
+           "batch_budget_ms": a.batch_budget_ms,
            "budget_gb": a.budget_gb, "geometries": sorted(geoms), "runs": []}
     for name, kw in modes:
         srv = Server(geoms, int(a.budget_gb * 2**30), n_streams=a.streams, **kw)
