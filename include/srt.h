@@ -215,6 +215,17 @@ int srt_stage_times(srt_plan_t plan, int32_t dir, float* ms, int32_t n);
 /* Number of kernel launches one srt_forward / srt_adjoint call makes. */
 int srt_launches_per_call(srt_plan_t plan, int32_t dir, int32_t batch);
 
+/*
+ * Measurement helper (no counterpart in the paper): the FP32 FMA rate the
+ * CUDA cores of the current GPU sustain, in TFLOP/s, from a kernel of
+ * independent FMA chains (8 blocks of 256 threads per SM, 16 chains per
+ * thread, iters FMAs per chain) timed with CUDA events on `stream` after one
+ * warm-up launch.  Synchronous.  This is the arithmetic roof of the sparse
+ * products (Sec. 3.1 products run on the CUDA cores, not tensor cores).
+ * Errors: SRT_ERR_ARG (null tflops, iters <= 0), SRT_ERR_CUDA.
+ */
+int srt_fp32_fma_peak(int32_t iters, double* tflops, void* stream);
+
 /* Release the plan's device memory.  NULL is accepted.  Not stream-ordered:
  * the caller must ensure no work using the plan is still in flight. */
 int srt_plan_destroy(srt_plan_t plan);

@@ -62,6 +62,7 @@ SIGNATURES = {
     "srt_plan_set_timing": (ctypes.c_int, [_VP, _I32]),
     "srt_stage_times": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_float), _I32]),
     "srt_launches_per_call": (ctypes.c_int, [_VP, _I32, _I32]),
+    "srt_fp32_fma_peak": (ctypes.c_int, [_I32, ctypes.POINTER(ctypes.c_double), _VP]),
     "srt_plan_destroy": (ctypes.c_int, [_VP]),
     "srt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -239,3 +239,11 @@ def dot_f64(a: torch.Tensor, b: torch.Tensor, stream=None) -> float:
                           (ws.numel() - 1) * 8, ctypes.c_void_p(_stream_ptr(stream))),
           "srt_dot_f64")
     return float(out.item())
+
+
+def fp32_fma_peak(iters: int = 20000, stream=None) -> float:
+    """Sustained FP32 FMA rate of the current GPU's CUDA cores, TFLOP/s."""
+    out = ctypes.c_double()
+    check(L.lib().srt_fp32_fma_peak(iters, ctypes.byref(out),
+                                    ctypes.c_void_p(_stream_ptr(stream))), "srt_fp32_fma_peak")
+    return out.value

@@ -60,7 +60,9 @@ def test_srt128_sampled(srt, orc):
     f = I.phantom("srt128")
     y = I.probe("srt128")
     sh, vx = _samples(g, 2048, 48, 31)
-    _check(srt, orc, plan, o, f, y, sh, vx, 1e-5)
+    e_p, e_a = _check(srt, orc, plan, o, f, y, sh, vx, 1e-5)
+    print(f"PARITY srt128 fp32 (2048 shells, 48 voxels): forward rel-L2 {e_p:.3e}, "
+          f"adjoint rel-L2 {e_a:.3e}")
     fd, yd = to_dev(f), to_dev(y)
     af, aty = plan.forward(fd), plan.adjoint(yd)
     lhs, rhs = srt.dot_f64(af, yd), srt.dot_f64(fd, aty)
@@ -81,8 +83,25 @@ def test_srt256_crop_sampled(srt, orc, srt256_inputs, wdt, tol, toep):
     f, y = srt256_inputs
     sh, vx = _samples(g, 4096, 96, 41, crop=64)
     e_p, e_a = _check(srt, orc, plan, o, f, y, sh, vx, tol)
-    print(f"srt256 {wdt}: forward rel-L2 {e_p:.3e}, adjoint rel-L2 {e_a:.3e}")
+    print(f"PARITY srt256 {wdt}{' toeplitz' if toep else ''} (64^3 crop, 4096 shells, 96 voxels):"
+          f" forward rel-L2 {e_p:.3e}, adjoint rel-L2 {e_a:.3e}")
     fd, yd = to_dev(f), to_dev(y)
     af, aty = plan.forward(fd), plan.adjoint(yd)
     lhs, rhs = srt.dot_f64(af, yd), srt.dot_f64(fd, aty)
     assert abs(lhs - rhs) / math.sqrt(srt.dot_f64(af, af) * srt.dot_f64(yd, yd)) <= 1e-6
+
+
+def test_srt256_bf16_against_fp32(srt, orc, srt256_inputs):
+    """The precision comparison at 256^3: BF16-stored entries against FP32
+    entries over the whole output (both FP32-accumulated)."""
+    sz = dict(I.sizes("srt256"))
+    g32, _ = geom_pair(orc, **sz)
+    g16, _ = geom_pair(orc, weight_dtype="bf16", **sz)
+    f, y = srt256_inputs
+    fd, yd = to_dev(f), to_dev(y)
+    a, b = srt.Plan(g32), srt.Plan(g16)
+    e_p = rel_l2(to_np(b.forward(fd)), to_np(a.forward(fd)))
+    e_a = rel_l2(to_np(b.adjoint(yd)), to_np(a.adjoint(yd)))
+    print(f"PARITY srt256 bf16 vs fp32 entries (full output): forward rel-L2 {e_p:.3e}, "
+          f"adjoint rel-L2 {e_a:.3e}")
+    assert 1e-5 < e_p <= 5e-3 and 1e-5 < e_a <= 5e-3

@@ -106,6 +106,8 @@ def test_forward_adjoint_c0(srt, orc, c0, wdt, tol):
     plan = srt.Plan(g)
     p_gpu = to_np(plan.forward(to_dev(f)))
     f_gpu = to_np(plan.adjoint(to_dev(y)))
+    print(f"PARITY srt32 {wdt}: forward rel-L2 {rel_l2(p_gpu, pf):.3e}, "
+          f"adjoint rel-L2 {rel_l2(f_gpu, fa):.3e}")
     assert rel_l2(p_gpu, pf) <= tol
     assert rel_l2(f_gpu, fa) <= tol
     if wdt == "fp32":  # the BF16 error is large enough to be seen at all
@@ -125,6 +127,8 @@ def test_adjoint_identity_on_gpu(srt, orc, name):
     lhs = srt.dot_f64(af, y)
     rhs = srt.dot_f64(f, aty)
     nrm = math.sqrt(srt.dot_f64(af, af) * srt.dot_f64(y, y))
+    print(f"PARITY {name} fp32: adjoint identity {abs(lhs - rhs) / nrm:.3e} "
+          f"(/|<Af,g>| {abs(lhs - rhs) / abs(lhs):.3e})")
     assert abs(lhs - rhs) / nrm <= ADJ_TOL
     # the FP64 device dot agrees with a host FP64 dot of the same floats
     assert lhs == pytest.approx(float(np.dot(to_np(af).ravel(), to_np(y).ravel())), rel=1e-12)
