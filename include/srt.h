@@ -142,10 +142,15 @@ int srt_adjoint(srt_plan_t plan, const float* p, float* f, int32_t batch, void* 
 /*
  * End-to-end variants on HOST buffers (same layouts as above; pinned memory
  * gives full copy speed).  The call copies the input to the device, runs the
- * transform in `workspace`, copies the result back and synchronises the
- * stream.  `workspace` must hold srt_host_workspace_bytes(batch) bytes of
- * device memory (device copies of input and output plus the transform
- * workspace).  Errors: as srt_forward.
+ * transform in `workspace` and copies the result back, then synchronises.
+ * The result is copied back in four chunks on a copy stream the call creates,
+ * each as soon as the transform has produced it (the forward's second product
+ * and reshape, and the adjoint's A1^T product, run in four row ranges), so
+ * most of the device-to-host copy overlaps the computation; results are
+ * bitwise those of srt_forward / srt_adjoint.  These calls record no
+ * per-stage timing.  `workspace` must hold srt_host_workspace_bytes(batch)
+ * bytes of device memory (device copies of input and output plus the
+ * transform workspace).  Errors: as srt_forward.
  */
 int srt_host_workspace_bytes(srt_plan_t plan, int32_t batch, size_t* bytes);
 int srt_forward_host(srt_plan_t plan, const float* f_host, float* p_host, int32_t batch,

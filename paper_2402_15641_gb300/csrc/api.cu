@@ -70,74 +70,130 @@ int check_ws(srt_plan_s* p, int batch, const void* ws, size_t ws_bytes) {
   return SRT_OK;
 }
 
+// Destination of a host-buffer call: the result is copied to `host` in
+// chunks on the copy stream `cs` as the chunks are produced on the compute
+// stream, so the copies overlap the rest of the transform.
+constexpr int kHostChunks = 4;
+struct HostSink {
+  float* host = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[kHostChunks] = {};
+};
+
+// Rows [r0, r0 + n) of A as a matrix of its own (row pointers stay absolute).
+SrtCsr rows_view(const SrtCsr& A, int64_t r0, int64_t n) {
+  SrtCsr v = A;
+  v.rows = (int32_t)n;
+  v.rowptr = A.rowptr + r0;
+  return v;
+}
+
+// Copy `height` rows of `width_elems` floats, `pitch_elems` apart, from the
+// device to the host on the sink's copy stream once the compute stream has
+// reached this point.
+int sink_copy(HostSink* hs, int chunk, cudaStream_t st, float* host, const float* dev,
+              int64_t width_elems, int64_t pitch_elems, int64_t height) {
+  SRT_CUDA_TRY(cudaEventRecord(hs->ev[chunk], st));
+  SRT_CUDA_TRY(cudaStreamWaitEvent(hs->cs, hs->ev[chunk], 0));
+  SRT_CUDA_TRY(cudaMemcpy2DAsync(host, pitch_elems * 4, dev, pitch_elems * 4, width_elems * 4,
+                                 height, cudaMemcpyDeviceToHost, hs->cs));
+  return SRT_OK;
+}
+
+// Forward (Algorithm 1).  With a sink, the second product and the final
+// reshape run in kHostChunks ring ranges and each range of p is copied to
+// the host while the next one is computed (no per-stage timing then).
 int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, float* w1,
-                cudaStream_t st) {
+                cudaStream_t st, HostSink* hs = nullptr) {
   const srt_geometry& g = p->g;
   const int64_t pix = (int64_t)g.ms * g.ms, r1 = (int64_t)g.n_phi * g.n_ell;
   const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
   const int64_t nb = (int64_t)B * g.n_phi;  // dense width of the second stage
-  mark(p, 0, 0, st);
+  if (!hs) mark(p, 0, 0, st);
   // Y1[b][j][l][k] = A1 F_b (CRT in the first plane, all slabs at once)
   // rows (j, l) visited radius-chunk-major across sensor columns (L2 reuse of F)
   SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B, st,
                    g.n_phi, g.n_ell));
-  mark(p, 0, 1, st);
+  if (!hs) mark(p, 0, 1, st);
   if (p->toeplitz) {
     // slabs Y1'[l][z][n] in tiles, then the vertical CRT as a z-correlation
     // written straight into p[b][j][h][m]
     SRT_TRY(srt_tiles_from_rows(w0, g.n_ell, g.mz, (int)nb, w1, st));
-    mark(p, 0, 2, st);
+    if (!hs) mark(p, 0, 2, st);
     SRT_TRY(srt_toep_apply(p->tf, g.weight_dtype, g.mz, g.mz - 1, g.n_ell, (int)nb, w1, out,
                            r2, g.n_ell, 1, st));
-    mark(p, 0, 3, st);
+    if (!hs) mark(p, 0, 3, st);
+    if (hs) {
+      const int64_t n = (int64_t)B * g.n_phi * r2;
+      SRT_TRY(sink_copy(hs, 0, st, hs->host, out, n, n, 1));
+    }
   } else {
     SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
-    mark(p, 0, 2, st);
+    if (!hs) mark(p, 0, 2, st);
     // rows (h, m) visited radius-chunk-major across rings: blocks running at
     // the same time gather a narrow band of Y1' rows, which stays in L2.  A
     // block owns 4 rings x 2 radii: neighbouring rings gather shifted copies
     // of the same cells (A2 is Toeplitz in z), so its warps share L1 lines.
-    SRT_TRY(srt_spmm(p->a2, g.weight_dtype, w1, nb, 0, w0, nb, 0, (int)nb, 1, st, g.n_zs,
-                     g.n_ell, 4));
-    mark(p, 0, 3, st);
-    SRT_TRY(srt_transpose(w0, nb, g.n_phi, out, r2, (int64_t)g.n_phi * r2, (int)r2, g.n_phi, B, st));
+    const int nc = hs ? (g.n_zs < kHostChunks ? g.n_zs : kHostChunks) : 1;
+    for (int c = 0; c < nc; ++c) {
+      const int h0 = (int)((int64_t)g.n_zs * c / nc), h1 = (int)((int64_t)g.n_zs * (c + 1) / nc);
+      const int64_t ra = (int64_t)h0 * g.n_ell, rn = (int64_t)(h1 - h0) * g.n_ell;
+      SRT_TRY(srt_spmm(rows_view(p->a2, ra, rn), g.weight_dtype, w1, nb, 0, w0 + ra * nb, nb, 0,
+                       (int)nb, 1, st, h1 - h0, g.n_ell, 4));
+      if (!hs) mark(p, 0, 3, st);
+      SRT_TRY(srt_transpose(w0 + ra * nb, nb, g.n_phi, out + ra, r2, (int64_t)g.n_phi * r2,
+                            (int)rn, g.n_phi, B, st));
+      if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra, out + ra, rn, r2, (int64_t)B * g.n_phi));
+    }
   }
-  mark(p, 0, 4, st);
-  if (p->timing) p->have_times[0] = 1;
+  if (!hs) {
+    if (!hs) mark(p, 0, 4, st);
+    if (p->timing) p->have_times[0] = 1;
+  }
   return SRT_OK;
 }
 
+// Adjoint (Algorithm 2).  With a sink, the last product (A1^T) runs in
+// kHostChunks ranges of pixel columns ix and each range of f is copied to the
+// host while the next one is computed (no per-stage timing then).
 int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, float* w1,
-                cudaStream_t st) {
+                cudaStream_t st, HostSink* hs = nullptr) {
   const srt_geometry& g = p->g;
   const int64_t pix = (int64_t)g.ms * g.ms, r1 = (int64_t)g.n_phi * g.n_ell;
   const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
   const int64_t nb = (int64_t)B * g.n_phi;
-  mark(p, 1, 0, st);
+  if (!hs) mark(p, 1, 0, st);
   const float* f1;  // F1[b][j][l][k], input of A1^T
   if (p->toeplitz) {
     // slabs P'[m][h][n] in tiles, then A2^T as a z-correlation written
     // straight into F1[b][j][l][k]
     SRT_TRY(srt_tiles_from_cols(in, g.n_ell, g.n_zs, (int)nb, w0, st));
-    mark(p, 1, 1, st);
+    if (!hs) mark(p, 1, 1, st);
     SRT_TRY(srt_toep_apply(p->ta, g.weight_dtype, g.mz, g.mz - 1, g.n_ell, (int)nb, w0, w1,
                            c1, 1, g.mz, st));
-    mark(p, 1, 2, st);
+    if (!hs) mark(p, 1, 2, st);
     f1 = w1;
   } else {
     SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
-    mark(p, 1, 1, st);
+    if (!hs) mark(p, 1, 1, st);
     SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));
-    mark(p, 1, 2, st);
+    if (!hs) mark(p, 1, 2, st);
     SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
     f1 = w0;
   }
-  mark(p, 1, 3, st);
+  if (!hs) mark(p, 1, 3, st);
   // rows (pixels) in blocks of 4 x 2 pixels: a circle crossing a compact
   // tile touches more of its pixels than of a line of 8, so warps share L1
-  SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f, g.mz, pix * g.mz, g.mz, B, st,
-                   g.ms, g.ms, 4));
-  mark(p, 1, 4, st);
+  const int nc = hs ? (g.ms < kHostChunks ? g.ms : kHostChunks) : 1;
+  for (int c = 0; c < nc; ++c) {
+    const int x0 = (int)((int64_t)g.ms * c / nc), x1 = (int)((int64_t)g.ms * (c + 1) / nc);
+    const int64_t ra = (int64_t)x0 * g.ms, rn = (int64_t)(x1 - x0) * g.ms;
+    SRT_TRY(srt_spmm(rows_view(p->a1t, ra, rn), g.weight_dtype, f1, g.mz, r1 * g.mz,
+                     f + ra * g.mz, g.mz, pix * g.mz, g.mz, B, st, x1 - x0, g.ms, 4));
+    if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra * g.mz, f + ra * g.mz, rn * g.mz, pix * g.mz, B));
+  }
+  if (hs) return SRT_OK;
+  if (!hs) mark(p, 1, 4, st);
   if (p->timing) p->have_times[1] = 1;
   return SRT_OK;
 }
@@ -260,17 +316,32 @@ static int host_call(srt_plan_t p, int dir, const float* in_h, float* out_h, int
   float* w0 = dp + align256(np * 4) / 4;
   float* w1 = w0 + align256(buf_elems(g, batch) * 4) / 4;
   cudaStream_t st = S(stream);
-  if (dir == 0) {
-    SRT_CUDA_TRY(cudaMemcpyAsync(df, in_h, nf * 4, cudaMemcpyHostToDevice, st));
-    SRT_TRY(run_forward(p, df, dp, batch, w0, w1, st));
-    SRT_CUDA_TRY(cudaMemcpyAsync(out_h, dp, np * 4, cudaMemcpyDeviceToHost, st));
-  } else {
-    SRT_CUDA_TRY(cudaMemcpyAsync(dp, in_h, np * 4, cudaMemcpyHostToDevice, st));
-    SRT_TRY(run_adjoint(p, dp, df, batch, w0, w1, st));
-    SRT_CUDA_TRY(cudaMemcpyAsync(out_h, df, nf * 4, cudaMemcpyDeviceToHost, st));
+  // results go back in chunks on a copy stream of this call, overlapping the
+  // rest of the transform
+  HostSink hs;
+  hs.host = out_h;
+  SRT_CUDA_TRY(cudaStreamCreateWithFlags(&hs.cs, cudaStreamNonBlocking));
+  int s = SRT_OK;
+  for (int i = 0; i < kHostChunks && s == SRT_OK; ++i)
+    if (cudaEventCreateWithFlags(&hs.ev[i], cudaEventDisableTiming) != cudaSuccess) s = SRT_ERR_CUDA;
+  if (s == SRT_OK) {
+    if (dir == 0) {
+      s = cudaMemcpyAsync(df, in_h, nf * 4, cudaMemcpyHostToDevice, st) == cudaSuccess
+              ? run_forward(p, df, dp, batch, w0, w1, st, &hs)
+              : SRT_ERR_CUDA;
+    } else {
+      s = cudaMemcpyAsync(dp, in_h, np * 4, cudaMemcpyHostToDevice, st) == cudaSuccess
+              ? run_adjoint(p, dp, df, batch, w0, w1, st, &hs)
+              : SRT_ERR_CUDA;
+    }
   }
-  SRT_CUDA_TRY(cudaStreamSynchronize(st));
-  return SRT_OK;
+  // wait for both streams whatever happened, then release them
+  if (cudaStreamSynchronize(st) != cudaSuccess && s == SRT_OK) s = SRT_ERR_CUDA;
+  if (cudaStreamSynchronize(hs.cs) != cudaSuccess && s == SRT_OK) s = SRT_ERR_CUDA;
+  for (int i = 0; i < kHostChunks; ++i)
+    if (hs.ev[i]) cudaEventDestroy(hs.ev[i]);
+  cudaStreamDestroy(hs.cs);
+  return s;
 }
 
 int srt_forward_host(srt_plan_t p, const float* f_host, float* p_host, int32_t batch, void* ws,
