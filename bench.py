@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--workload", default="srt256")
     p.add_argument("--weights", choices=["fp32", "bf16"], default="fp32")
     p.add_argument("--batch", type=int, default=1)
+    p.add_argument("--csr-only", action="store_true",
+                   help="store A2, A2^T as CSR instead of applying them from the Toeplitz taps")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
     return p.parse_args()
@@ -163,9 +165,14 @@ def stage_model(geom, info, batch, weights):
     fv = 4 * batch * pix * geom.mz          # bytes of f
     spmm1 = dict(flop=2 * nnz1 * geom.mz * batch,
                  bytes=nnz1 * (vb + 4) + 4 * (r1 + 1) + fv + y1)
-    spmm2 = dict(flop=2 * nnz2 * geom.n_phi * batch,
-                 bytes=nnz2 * (vb + 4) + 4 * (r2 + 1) + y1 + pp)
-    spmm2t = dict(flop=spmm2["flop"], bytes=nnz2 * (vb + 4) + 4 * (c1 + 1) + pp + y1)
+    if info.get("a2_taps"):  # A2 held by the taps of T: key + value per tap, sub-row pointers
+        sub = 4 * (geom.n_ell * (2 * geom.mz - 1) + 1)
+        a2b = a2tb = info["n_taps"] * (vb + 4) + sub
+    else:
+        a2b = nnz2 * (vb + 4) + 4 * (r2 + 1)
+        a2tb = nnz2 * (vb + 4) + 4 * (c1 + 1)
+    spmm2 = dict(flop=2 * nnz2 * geom.n_phi * batch, bytes=a2b + y1 + pp)
+    spmm2t = dict(flop=spmm2["flop"], bytes=a2tb + pp + y1)
     spmm1t = dict(flop=spmm1["flop"], bytes=nnz1 * (vb + 4) + 4 * (pix + 1) + y1 + fv)
     p1 = dict(flop=0, bytes=2 * y1)
     p2 = dict(flop=0, bytes=2 * pp)
@@ -307,7 +314,7 @@ def run_ours(args):
     build.build()
     pk = peaks()
     sz = I.sizes(args.workload)
-    geom = Geometry.from_sizes(sz, weight_dtype=args.weights)
+    geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only)
     B = args.batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -422,7 +429,10 @@ def run_ours(args):
                                      {"l2": "flushed between steps (256 MiB write, untimed)",
                                       "parallelism": "replicas" if world > 1 else "single GPU",
                                       "plan_build_s": round(plan_s, 3),
-                                      "nnz1": plan.info["nnz1"], "nnz2": plan.info["nnz2"]}),
+                                      "nnz1": plan.info["nnz1"], "nnz2": plan.info["nnz2"],
+                                      "a2_form": (f"Toeplitz taps ({plan.info['n_taps']} taps of T)"
+                                                  if plan.info["a2_taps"] else "CSR"),
+                                      "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3)}),
            "roofline": roof, "hbm": hbm, "stages": stages, "clocks": clk, "e2e": e2e,
            "gpu_launches": launches}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -47,8 +47,11 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
 
 /* Plan flags. */
 #define SRT_KEEP_F64 0x1 /* keep FP64 copies of A1/A2 entries for srt_plan_export */
-#define SRT_CSR_ONLY 0x2 /* apply every product from plain CSR                       */
-#define SRT_TOEPLITZ 0x4 /* second stage as a z-correlation (rings at slab centres) */
+#define SRT_CSR_ONLY 0x2 /* store A2, A2^T as CSR even when the taps would serve   */
+/* When the rings sit at the slab centres (n_zs = mz over the volume height),
+ * A2[(h,m),(l,k)] = T[m, k-h, l] for a master tensor T, and the plan applies A2
+ * and A2^T from T's taps without storing them (srt_plan_info_t.a2_taps = 1),
+ * unless SRT_CSR_ONLY is set. */
 
 /*
  * Geometry (Sec. 3.1, Algorithm 1 inputs).  Lengths in mm, angles in rad.
@@ -86,7 +89,8 @@ typedef struct srt_plan_info_t {
   int64_t dropped1, dropped2; /* entries with 0 < length <= 1e-12 spacing     */
   int64_t device_bytes;       /* device memory owned by the plan              */
   int32_t weight_dtype;
-  int32_t reserved;
+  int32_t a2_taps;            /* 1: A2, A2^T applied from Toeplitz taps       */
+  int64_t n_taps;             /* taps of the master tensor T (0 for CSR A2)   */
 } srt_plan_info_t;
 
 /*

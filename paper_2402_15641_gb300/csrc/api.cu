@@ -20,14 +20,11 @@ inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline int64_t align256(int64_t b) { return (b + 255) & ~(int64_t)255; }
 
-// Elements of one intermediate buffer: the largest of Y1, P' and the tiled
-// slabs of the second stage, whose dense columns are padded to a multiple of
-// SRT_TOEP_NC.
+// Elements of one intermediate buffer: the larger of Y1 (= Y1') and P'.
 int64_t buf_elems(const srt_geometry& g, int batch) {
   const int64_t nb = (int64_t)batch * g.n_phi;
-  const int64_t nb4 = (nb + SRT_TOEP_NC - 1) / SRT_TOEP_NC * SRT_TOEP_NC;
   const int64_t zmax = g.mz > g.n_zs ? g.mz : g.n_zs;
-  return nb4 * g.n_ell * zmax;
+  return nb * g.n_ell * zmax;
 }
 
 int check_geometry(const srt_geometry& g) {
@@ -54,6 +51,7 @@ void free_plan(srt_plan_s* p) {
   srt_csr_free(&p->a2t);
   srt_taps_free(&p->tf);
   srt_taps_free(&p->ta);
+  srt_csr_free(&p->tm);
   for (int d = 0; d < 2; ++d)
     for (int i = 0; i < 5; ++i)
       if (p->ev[d][i]) cudaEventDestroy(p->ev[d][i]);
@@ -115,39 +113,29 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B, st,
                    g.n_phi, g.n_ell));
   if (!hs) mark(p, 0, 1, st);
-  if (p->toeplitz) {
-    // slabs Y1'[l][z][n] in tiles, then the vertical CRT as a z-correlation
-    // written straight into p[b][j][h][m]
-    SRT_TRY(srt_tiles_from_rows(w0, g.n_ell, g.mz, (int)nb, w1, st));
-    if (!hs) mark(p, 0, 2, st);
-    SRT_TRY(srt_toep_apply(p->tf, g.weight_dtype, g.mz, g.mz - 1, g.n_ell, (int)nb, w1, out,
-                           r2, g.n_ell, 1, st));
-    if (!hs) mark(p, 0, 3, st);
-    if (hs) {
-      const int64_t n = (int64_t)B * g.n_phi * r2;
-      SRT_TRY(sink_copy(hs, 0, st, hs->host, out, n, n, 1));
-    }
-  } else {
-    SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
-    if (!hs) mark(p, 0, 2, st);
-    // rows (h, m) visited radius-chunk-major across rings: blocks running at
-    // the same time gather a narrow band of Y1' rows, which stays in L2.  A
-    // block owns 4 rings x 2 radii: neighbouring rings gather shifted copies
-    // of the same cells (A2 is Toeplitz in z), so its warps share L1 lines.
-    const int nc = hs ? (g.n_zs < kHostChunks ? g.n_zs : kHostChunks) : 1;
-    for (int c = 0; c < nc; ++c) {
-      const int h0 = (int)((int64_t)g.n_zs * c / nc), h1 = (int)((int64_t)g.n_zs * (c + 1) / nc);
-      const int64_t ra = (int64_t)h0 * g.n_ell, rn = (int64_t)(h1 - h0) * g.n_ell;
+  SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
+  if (!hs) mark(p, 0, 2, st);
+  // rows (h, m) visited radius-chunk-major across rings: blocks running at
+  // the same time gather a narrow band of Y1' rows, which stays in L2.  A
+  // block owns 4 rings x 2 radii: neighbouring rings gather shifted copies
+  // of the same cells (A2 is Toeplitz in z), so its warps share L1 lines.
+  const int nc = hs ? (g.n_zs < kHostChunks ? g.n_zs : kHostChunks) : 1;
+  for (int c = 0; c < nc; ++c) {
+    const int h0 = (int)((int64_t)g.n_zs * c / nc), h1 = (int)((int64_t)g.n_zs * (c + 1) / nc);
+    const int64_t ra = (int64_t)h0 * g.n_ell, rn = (int64_t)(h1 - h0) * g.n_ell;
+    if (p->toeplitz)  // A2 from the taps of the master tensor
+      SRT_TRY(srt_taps_apply(p, false, ra, rn, h1 - h0, g.n_ell, 4, w1, nb, w0 + ra * nb, nb,
+                             (int)nb, st));
+    else
       SRT_TRY(srt_spmm(rows_view(p->a2, ra, rn), g.weight_dtype, w1, nb, 0, w0 + ra * nb, nb, 0,
                        (int)nb, 1, st, h1 - h0, g.n_ell, 4));
-      if (!hs) mark(p, 0, 3, st);
-      SRT_TRY(srt_transpose(w0 + ra * nb, nb, g.n_phi, out + ra, r2, (int64_t)g.n_phi * r2,
-                            (int)rn, g.n_phi, B, st));
-      if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra, out + ra, rn, r2, (int64_t)B * g.n_phi));
-    }
+    if (!hs) mark(p, 0, 3, st);
+    SRT_TRY(srt_transpose(w0 + ra * nb, nb, g.n_phi, out + ra, r2, (int64_t)g.n_phi * r2,
+                          (int)rn, g.n_phi, B, st));
+    if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra, out + ra, rn, r2, (int64_t)B * g.n_phi));
   }
   if (!hs) {
-    if (!hs) mark(p, 0, 4, st);
+    mark(p, 0, 4, st);
     if (p->timing) p->have_times[0] = 1;
   }
   return SRT_OK;
@@ -163,24 +151,15 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
   const int64_t nb = (int64_t)B * g.n_phi;
   if (!hs) mark(p, 1, 0, st);
-  const float* f1;  // F1[b][j][l][k], input of A1^T
-  if (p->toeplitz) {
-    // slabs P'[m][h][n] in tiles, then A2^T as a z-correlation written
-    // straight into F1[b][j][l][k]
-    SRT_TRY(srt_tiles_from_cols(in, g.n_ell, g.n_zs, (int)nb, w0, st));
-    if (!hs) mark(p, 1, 1, st);
-    SRT_TRY(srt_toep_apply(p->ta, g.weight_dtype, g.mz, g.mz - 1, g.n_ell, (int)nb, w0, w1,
-                           c1, 1, g.mz, st));
-    if (!hs) mark(p, 1, 2, st);
-    f1 = w1;
-  } else {
-    SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
-    if (!hs) mark(p, 1, 1, st);
+  SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
+  if (!hs) mark(p, 1, 1, st);
+  if (p->toeplitz)  // A2^T from the taps of the master tensor
+    SRT_TRY(srt_taps_apply(p, true, 0, c1, 0, 0, 1, w0, nb, w1, nb, (int)nb, st));
+  else
     SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));
-    if (!hs) mark(p, 1, 2, st);
-    SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
-    f1 = w0;
-  }
+  if (!hs) mark(p, 1, 2, st);
+  SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
+  const float* f1 = w0;  // F1[b][j][l][k], input of A1^T
   if (!hs) mark(p, 1, 3, st);
   // rows (pixels) in blocks of 4 x 2 pixels: a circle crossing a compact
   // tile touches more of its pixels than of a line of 8, so warps share L1
@@ -193,7 +172,7 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
     if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra * g.mz, f + ra * g.mz, rn * g.mz, pix * g.mz, B));
   }
   if (hs) return SRT_OK;
-  if (!hs) mark(p, 1, 4, st);
+  mark(p, 1, 4, st);
   if (p->timing) p->have_times[1] = 1;
   return SRT_OK;
 }
@@ -265,7 +244,8 @@ int srt_plan_info(srt_plan_t p, srt_plan_info_t* o) {
   o->dropped2 = p->dropped2;
   o->device_bytes = p->bytes;
   o->weight_dtype = p->g.weight_dtype;
-  o->reserved = 0;
+  o->a2_taps = p->toeplitz;
+  o->n_taps = p->toeplitz ? p->tm.nnz : 0;
   return SRT_OK;
 }
 
@@ -363,12 +343,9 @@ int srt_dot_f64(const float* a, const float* b, int64_t n, double* out, void* ws
   return srt_dot(a, b, n, out, (double*)ws, S(stream));
 }
 
-int srt_plan_export(srt_plan_t p, int32_t which, int32_t* rowptr, int32_t* col, float* val32,
-                    double* val64) {
-  if (!p || !rowptr || !col) return SRT_ERR_ARG;
-  const SrtCsr* m = which == 1 ? &p->a1 : which == 2 ? &p->a2 : which == 3 ? &p->a1t
-                  : which == 4 ? &p->a2t : nullptr;
-  if (!m) return SRT_ERR_ARG;
+namespace {
+
+int export_csr(const SrtCsr* m, int32_t* rowptr, int32_t* col, float* val32, double* val64) {
   if (val64 && !m->v64) return SRT_ERR_ARG;
   SRT_CUDA_TRY(cudaMemcpy(rowptr, m->rowptr, ((size_t)m->rows + 1) * 4, cudaMemcpyDeviceToHost));
   SRT_CUDA_TRY(cudaMemcpy(col, m->col, (size_t)m->nnz * 4, cudaMemcpyDeviceToHost));
@@ -390,6 +367,26 @@ int srt_plan_export(srt_plan_t p, int32_t which, int32_t* rowptr, int32_t* col, 
     }
   }
   return SRT_OK;
+}
+
+}  // namespace
+
+int srt_plan_export(srt_plan_t p, int32_t which, int32_t* rowptr, int32_t* col, float* val32,
+                    double* val64) {
+  if (!p || !rowptr || !col) return SRT_ERR_ARG;
+  if (which < 1 || which > 4) return SRT_ERR_ARG;
+  if (which == 1 || which == 3 || !p->toeplitz)
+    return export_csr(which == 1 ? &p->a1 : which == 2 ? &p->a2 : which == 3 ? &p->a1t : &p->a2t,
+                      rowptr, col, val32, val64);
+  // A2 / A2^T of a plan that keeps only the Toeplitz taps: expand the master
+  // tensor into temporary CSR matrices
+  if (val64 && !p->tm.v64) return SRT_ERR_ARG;
+  SrtCsr a2, a2t;
+  int s = srt_expand_a2(p, &a2, which == 4 ? &a2t : nullptr, nullptr);
+  if (s == SRT_OK) s = export_csr(which == 2 ? &a2 : &a2t, rowptr, col, val32, val64);
+  srt_csr_free(&a2);
+  srt_csr_free(&a2t);
+  return s;
 }
 
 int srt_plan_set_timing(srt_plan_t p, int32_t enable) {
@@ -415,7 +412,7 @@ int srt_launches_per_call(srt_plan_t p, int32_t dir, int32_t batch) {
   (void)dir;
   (void)batch;
   if (!p) return 0;
-  return p->toeplitz ? 3 : 4;
+  return 4;
 }
 
 int srt_plan_destroy(srt_plan_t p) {

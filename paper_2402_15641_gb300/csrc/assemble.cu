@@ -473,8 +473,8 @@ void srt_csr_free(SrtCsr* m) {
 static bool toeplitz_applies(const srt_geometry& g) {
   const double h = g.mz * g.dz;
   return g.n_zs == g.mz && fabs(g.zs_lo + 0.5 * h) <= 1e-12 * h &&
-         fabs(g.zs_hi - 0.5 * h) <= 1e-12 * h && !(g.flags & SRT_CSR_ONLY) &&
-         (g.flags & SRT_TOEPLITZ);
+         fabs(g.zs_hi - 0.5 * h) <= 1e-12 * h && !(g.flags & SRT_CSR_ONLY) && g.n_ell <= 0xffff &&
+         2 * g.mz - 1 <= 0x7fff;
 }
 
 static int expand_toeplitz(const SrtCsr& T, const srt_geometry& g, SrtCsr* a2, int64_t* bytes,
@@ -500,7 +500,7 @@ static int expand_toeplitz(const SrtCsr& T, const srt_geometry& g, SrtCsr* a2, i
   SRT_TRY(srt_dmalloc(&a2->col, nnz, bytes));
   if (T.v32) SRT_TRY(srt_dmalloc(&a2->v32, nnz, bytes));
   if (T.v16) SRT_TRY(srt_dmalloc(&a2->v16, nnz, bytes));
-  SRT_TRY(srt_dmalloc(&a2->v64, nnz, nullptr));
+  if (T.v64) SRT_TRY(srt_dmalloc(&a2->v64, nnz, nullptr));
   k_expand_toeplitz<<<blocks, 256, 0, st>>>(g.mz, g.n_ell, rows, 1, T.rowptr, T.col, T.v32, T.v16,
                                             T.v64, nullptr, a2->rowptr, a2->col, a2->v32, a2->v16,
                                             a2->v64);
@@ -515,20 +515,28 @@ int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
   const int wdt = plan->g.weight_dtype;
   SRT_TRY(assemble_one<true>(G, wdt, &plan->a1, &plan->dropped1, &plan->bytes, st));
   if (toeplitz_applies(plan->g)) {
-    // master tensor: one ring at z = 0 over 2 mz - 1 slabs centred on it
+    // master tensor: one ring at z = 0 over 2 mz - 1 slabs centred on it;
+    // A2 and A2^T are applied from its taps and never stored as matrices
     GeomDev GT = G;
     GT.mz = 2 * G.mz - 1;
     GT.n_zs = 1;
     GT.zs_lo = -0.5 * G.dz;
     GT.zs_hi = 0.5 * G.dz;
     GT.hz = 0.5 * GT.mz * GT.dz;
-    SrtCsr T;
-    int s = assemble_one<false>(GT, wdt, &T, &plan->dropped2, nullptr, st);
-    if (s == SRT_OK) s = expand_toeplitz(T, plan->g, &plan->a2, &plan->bytes, st);
-    if (s == SRT_OK) s = srt_build_toeplitz(plan, T, &plan->bytes);
-    srt_csr_free(&T);
-    SRT_TRY(s);
+    SRT_TRY(assemble_one<false>(GT, wdt, &plan->tm, &plan->dropped2, &plan->bytes, st));
+    int64_t nnz2 = 0;
+    SRT_TRY(srt_build_taps(plan, plan->tm, &nnz2, &plan->bytes));
+    const srt_geometry& g = plan->g;
+    plan->a2.rows = plan->a2t.cols = g.n_zs * g.n_ell;
+    plan->a2.cols = plan->a2t.rows = g.n_ell * g.mz;
+    plan->a2.nnz = plan->a2t.nnz = nnz2;
     plan->toeplitz = 1;
+    if (!keep) {
+      cudaFree(plan->tm.v64);
+      plan->tm.v64 = nullptr;
+    } else {
+      plan->bytes += plan->tm.nnz * (int64_t)sizeof(double);
+    }
   } else {
     SRT_TRY(assemble_one<false>(G, wdt, &plan->a2, &plan->dropped2, &plan->bytes, st));
   }
@@ -537,9 +545,16 @@ int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
     cudaFree(plan->a2.v64);
     plan->a1.v64 = plan->a2.v64 = nullptr;
   } else {
-    plan->bytes += (plan->a1.nnz + plan->a2.nnz) * (int64_t)sizeof(double);
+    plan->bytes += (plan->a1.nnz + (plan->toeplitz ? 0 : plan->a2.nnz)) * (int64_t)sizeof(double);
   }
   SRT_TRY(transpose_csr(plan->a1, &plan->a1t, &plan->bytes, st));
-  SRT_TRY(transpose_csr(plan->a2, &plan->a2t, &plan->bytes, st));
+  if (!plan->toeplitz) SRT_TRY(transpose_csr(plan->a2, &plan->a2t, &plan->bytes, st));
+  return SRT_OK;
+}
+
+int srt_expand_a2(const srt_plan_s* plan, SrtCsr* a2, SrtCsr* a2t, cudaStream_t st) {
+  if (!plan->toeplitz) return SRT_ERR_ARG;
+  SRT_TRY(expand_toeplitz(plan->tm, plan->g, a2, nullptr, st));
+  if (a2t) SRT_TRY(transpose_csr(*a2, a2t, nullptr, st));
   return SRT_OK;
 }

@@ -35,33 +35,26 @@ struct SrtCsr {
   double* v64 = nullptr;      // nnz (SRT_KEEP_F64)
 };
 
-// Toeplitz form of A2, used when the rings sit at the slab centres
-// (n_zs = mz over the volume height): then A2[(h,m),(l,k)] = T[m, k-h, l] and
-// the second stage is, for every (m, l), a correlation along z.  Entries are
-// "taps" (offset d = k - h, band start o, weights) grouped per output block of
-// TB consecutive block indices and, inside a block, in segments sharing one
-// key (the input slab).  Forward: blocks over m, key = l, band over m.
-// Adjoint: blocks over l, key = m, band over l.  Values are T's entries,
-// i.e. bit-identical to the CSR form of A2.
-struct SrtTapList {
-  int32_t nblk = 0, W = 0, WP = 0;
-  int64_t nseg = 0, nent = 0;
-  int32_t* blk_seg = nullptr;  // nblk + 1: segment range of each block
-  int32_t* seg_key = nullptr;  // nseg: key (slab index) of the segment
-  int32_t* seg_ent = nullptr;  // nseg + 1: entry range of each segment
-  int32_t* meta = nullptr;     // nent: (uint16)d | (o << 16)
-  float* w32 = nullptr;        // nent * WP
-  uint16_t* w16 = nullptr;     // nent * WP
+// Toeplitz form of A2 (toeplitz.cu), used when the rings sit at the slab
+// centres: A2[(h,m),(l,k)] = T[m, k - h, l].  Taps grouped in sub-rows so that
+// every output row of A2 (forward) or A2^T (adjoint) is one contiguous range:
+// forward sub-rows (m, d + mz - 1) listing l, key l | (d + mz - 1) << 16;
+// adjoint sub-rows (l, mz - 1 - d) listing m, key m | (mz - 1 - d) << 16.
+struct SrtTaps {
+  int64_t nsub = 0, nent = 0;
+  int32_t* rowptr = nullptr;  // nsub + 1
+  int32_t* key = nullptr;     // nent
+  float* w32 = nullptr;       // nent (SRT_FP32)
+  uint16_t* w16 = nullptr;    // nent (SRT_BF16)
 };
-constexpr int SRT_TOEP_TB = 16;  // output indices per block
-constexpr int SRT_TOEP_NC = 4;   // dense columns per tile
 
 struct srt_plan_s {
   srt_geometry g;
   int device = 0;
   SrtCsr a1, a2, a1t, a2t;  // A1 = A^{1,2}, A2 = A^{3,4} and their transposes
-  int toeplitz = 0;         // second stage through the Toeplitz taps below
-  SrtTapList tf, ta;        // forward / adjoint taps of A2
+  int toeplitz = 0;         // second product through the Toeplitz taps below
+  SrtTaps tf, ta;           // forward / adjoint taps of A2 (a2, a2t then hold no arrays)
+  SrtCsr tm;                // master tensor T (rows m, columns l*(2mz-1) + d + mz - 1)
   int64_t dropped1 = 0, dropped2 = 0;
   int64_t bytes = 0;
   // per-stage timing (srt_plan_set_timing)
@@ -75,35 +68,21 @@ struct srt_plan_s {
 int srt_assemble(srt_plan_s* plan, cudaStream_t stream);
 void srt_csr_free(SrtCsr* m);
 
-// Build the forward/adjoint tap lists from the master tensor T (rows m, columns
-// l*(2 mz - 1) + (d + mz - 1)).
-int srt_build_toeplitz(srt_plan_s* plan, const SrtCsr& T, int64_t* bytes);
-void srt_taps_free(SrtTapList* t);
+// Build plan->tf / plan->ta from the master tensor T (rows m, columns
+// l*(2 mz - 1) + d + mz - 1); *nnz2 = number of entries of the A2 they stand for.
+int srt_build_taps(srt_plan_s* plan, const SrtCsr& T, int64_t* nnz2, int64_t* bytes);
+void srt_taps_free(SrtTaps* t);
+// Expand the master tensor into CSR A2 (and A2^T when a2t is given), for export.
+int srt_expand_a2(const srt_plan_s* plan, SrtCsr* a2, SrtCsr* a2t, cudaStream_t stream);
 
 // ------------------------------------------------------------- operators
-// Second stage through the tap lists.  x: tiles [key][chunk][pos][NC] (pos <
-// npos), out[n*sN + pos*sP + ob*sB] for output index ob = block*TB + t.
-int srt_toep_apply(const SrtTapList& L, int wdt, int npos, int halo, int nob, int ncols,
-                   const float* x, float* out, int64_t sN, int64_t sP, int64_t sB,
+// Rows [r0, r0 + rows) of A2 (adjoint = false; rows (h, m)) or A2^T
+// (adjoint = true; rows (l, k)) through the taps: y[r - r0][n] = sum over the
+// row's taps of w * x[gathered row][n], n < ncols.  Blocks visit the rows as
+// srt_spmm does with (G, R, TG).
+int srt_taps_apply(const srt_plan_s* plan, bool adjoint, int64_t r0, int64_t rows, int G, int R,
+                   int TG, const float* x, int64_t ldx, float* y, int64_t ldy, int ncols,
                    cudaStream_t stream);
-// Tiles for the second stage: out[key][c][pos][NC] from in[n][key][pos]
-// (rows, fwd) or in[n][pos][key] (cols, adj); n = c*NC + lane, zero past ncols.
-int srt_tiles_from_rows(const float* in, int nkey, int npos, int ncols, float* out,
-                        cudaStream_t stream);
-int srt_tiles_from_cols(const float* in, int nkey, int npos, int ncols, float* out,
-                        cudaStream_t stream);
-
-// Second stage through the tap lists.  x: tiles [key][chunk][pos][NC] (pos <
-// npos), out[n*sN + pos*sP + ob*sB] for output index ob = block*TB + t.
-int srt_toep_apply(const SrtTapList& L, int wdt, int npos, int halo, int nob, int ncols,
-                   const float* x, float* out, int64_t sN, int64_t sP, int64_t sB,
-                   cudaStream_t stream);
-// Tiles for the second stage: out[key][c][pos][NC] from in[n][key][pos]
-// (rows, fwd) or in[n][pos][key] (cols, adj); n = c*NC + lane, zero past ncols.
-int srt_tiles_from_rows(const float* in, int nkey, int npos, int ncols, float* out,
-                        cudaStream_t stream);
-int srt_tiles_from_cols(const float* in, int nkey, int npos, int ncols, float* out,
-                        cudaStream_t stream);
 
 // y[b][r][n] = sum_e A[r, col[e]] * x[b][col[e]][n] for n < ncols.  With G > 0
 // the rows (G groups of R) are visited chunk-major across groups, a block

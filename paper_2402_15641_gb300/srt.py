@@ -40,12 +40,11 @@ class Geometry:
     weight_dtype: str = "fp32"  # "fp32" | "bf16"
     keep_f64: bool = False
     csr_only: bool = False
-    toeplitz: bool = False
 
     @staticmethod
     def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, **options) -> "Geometry":
         """Default readings, computed by the library (srt_geometry_default);
-        options set weight_dtype / keep_f64 / csr_only / toeplitz."""
+        options set weight_dtype / keep_f64 / csr_only."""
         g = L.SrtGeometry()
         check(L.lib().srt_geometry_default(ctypes.byref(g), ms, mz, dxy, dz, radius, n_phi, n_zs,
                                            n_ell), "srt_geometry_default")
@@ -66,8 +65,7 @@ class Geometry:
                              self.phi0, self.n_zs, self.zs_lo, self.zs_hi, self.n_ell,
                              self.ell_lo, self.ell_hi, wd,
                              (L.SRT_KEEP_F64 if self.keep_f64 else 0)
-                             | (L.SRT_CSR_ONLY if self.csr_only else 0)
-                             | (L.SRT_TOEPLITZ if self.toeplitz else 0))
+                             | (L.SRT_CSR_ONLY if self.csr_only else 0))
 
     @property
     def f_shape(self):
@@ -109,7 +107,7 @@ class Plan:
         self._ws = {}
         info = L.SrtPlanInfo()
         check(self._lib.srt_plan_info(self._h, ctypes.byref(info)), "srt_plan_info")
-        self.info = {k: getattr(info, k) for k, _ in L.SrtPlanInfo._fields_ if k != "reserved"}
+        self.info = {k: getattr(info, k) for k, _ in L.SrtPlanInfo._fields_}
 
     # -------------------------------------------------------------- memory
     def workspace_bytes(self, batch: int = 1) -> int:

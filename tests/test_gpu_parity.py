@@ -174,6 +174,46 @@ def test_fd16_full_and_batched_bitwise(srt, orc):
     assert rel_l2(to_np(ab[1]), orc.adjoint(o, y[1])) <= FP32_TOL
 
 
+@pytest.mark.parametrize("wdt", ["fp32", "bf16"])
+def test_batch16_bitwise_per_volume(srt, orc, wdt):
+    """Batch 16 at 32^3: the second product's dense width is 16 x 64 = 1024
+    columns (the 512-column kernel), the first product runs 16 volumes per
+    launch; every batch item equals the single-volume result bitwise."""
+    import torch
+    g, o = geom_pair(orc, weight_dtype=wdt, **dict(I.sizes("srt32")))
+    plan = srt.Plan(g)
+    rng = np.random.default_rng(12)
+    f = rng.uniform(0, 1, (16, *g.f_shape))
+    y = rng.standard_normal((16, *g.p_shape))
+    pb = plan.forward(to_dev(f))
+    ab = plan.adjoint(to_dev(y))
+    for b in (0, 5, 15):
+        assert torch.equal(plan.forward(to_dev(f[b])), pb[b])
+        assert torch.equal(plan.adjoint(to_dev(y[b])), ab[b])
+    tol = FP32_TOL if wdt == "fp32" else BF16_TOL
+    assert rel_l2(to_np(pb[15]), orc.forward(o, f[15])) <= tol
+    assert rel_l2(to_np(ab[7]), orc.adjoint(o, y[7])) <= tol
+
+
+@pytest.mark.parametrize("sz", [RAGGED[0], RAGGED[3], dict(I.sizes("srt32"))])
+def test_host_calls_chunked_equal_device(srt, orc, sz):
+    """The host-buffer calls compute the last product in row ranges and copy
+    each back while the next is computed: results equal the device path
+    bitwise, also when there are fewer rings or pixel columns than chunks."""
+    import torch
+    g, _ = geom_pair(orc, **sz)
+    plan = srt.Plan(g)
+    rng = np.random.default_rng(13)
+    f = torch.from_numpy(rng.uniform(0, 1, (2, *g.f_shape)).astype(np.float32)).pin_memory()
+    y = torch.from_numpy(rng.standard_normal((2, *g.p_shape)).astype(np.float32)).pin_memory()
+    p_h = torch.full((2, *g.p_shape), float("nan"), dtype=torch.float32).pin_memory()
+    f_h = torch.full((2, *g.f_shape), float("nan"), dtype=torch.float32).pin_memory()
+    plan.forward_host(f, p_h)
+    plan.adjoint_host(y, f_h)
+    assert torch.equal(p_h, plan.forward(f.cuda()).cpu())
+    assert torch.equal(f_h, plan.adjoint(y.cuda()).cpu())
+
+
 def test_host_buffer_variants_equal_device(srt, orc):
     import torch
     g, _ = geom_pair(orc, **dict(I.sizes("srt16fd")))
@@ -221,13 +261,18 @@ TOEP = [dict(I.sizes("srt32")), dict(I.sizes("srt16fd")),
 @pytest.mark.parametrize("sz", TOEP)
 @pytest.mark.parametrize("wdt", ["fp32", "bf16"])
 def test_toeplitz_second_stage(srt, orc, sz, wdt):
-    """With the rings at the slab centres the second stage runs as a
-    z-correlation of the master tensor T (A2 = T shifted per ring); it applies
-    the same stored entries as the CSR product, bit for bit (exported A2 is
-    compared), and matches the oracle."""
-    g, o = geom_pair(orc, weight_dtype=wdt, toeplitz=True, **sz)
+    """With the rings at the slab centres A2 and A2^T are applied from the
+    taps of the master tensor T (A2 = T shifted per ring) and never stored:
+    the A2 they stand for (exported by expanding T) has the pattern of the
+    directly assembled one and its entries to FP64 rounding, the plan is
+    smaller by A2 and A2^T, and the transforms match the CSR plan and the
+    oracle (dense widths 5 and 15 take the scalar kernel)."""
+    g, o = geom_pair(orc, weight_dtype=wdt, **sz)
     a = srt.Plan(g)
-    b = srt.Plan(g.with_(toeplitz=False, csr_only=True))
+    b = srt.Plan(g.with_(csr_only=True))
+    assert a.info["a2_taps"] == 1 and a.info["n_taps"] > 0 and b.info["a2_taps"] == 0
+    assert a.info["nnz2"] == b.info["nnz2"]
+    assert a.info["device_bytes"] < b.info["device_bytes"]
     for which in (2, 4):
         ra, ca, va, _ = a.export(which)
         rb, cb, vb, _ = b.export(which)
@@ -266,7 +311,9 @@ def test_plan_info_and_timing(srt, orc):
     from paper_2402_15641_gb300._lib import SrtError
     with pytest.raises(SrtError):
         plan.stage_times(1)
-    assert plan.launches_per_call(0) == 4
-    t = srt.Plan(g.with_(toeplitz=True))
-    assert t.launches_per_call(0) == 3 and t.launches_per_call(1) == 3
+    assert plan.launches_per_call(0) == 4 and plan.launches_per_call(1) == 4
+    assert inf["a2_taps"] == 1  # rings at the slab centres: A2 from the taps
+    c = srt.Plan(g.with_(csr_only=True))
+    assert c.info["a2_taps"] == 0 and c.info["n_taps"] == 0
+    assert c.launches_per_call(0) == 4 and c.launches_per_call(1) == 4
     torch.cuda.synchronize()

@@ -106,7 +106,7 @@ def test_host_side_failures(env):
     assert r_cancel.result is None and r_cancel.cancelled
     assert srv.stats.failed == 4 and srv.stats.cancelled == 1
     srv.close()
-    tiny = SV.Server({"a": geoms["a"]}, budget_bytes=1 << 20)
+    tiny = SV.Server({"a": geoms["a"]}, budget_bytes=16 << 10)  # below any plan
     r = tiny.submit("a", "fwd", payloads[("a", "fwd")][0])
     tiny.drain()
     assert r.error and "budget" in r.error
