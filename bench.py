@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--batch", type=int, default=1)
     p.add_argument("--csr-only", action="store_true",
                    help="store A2, A2^T as CSR instead of applying them from the Toeplitz taps")
+    p.add_argument("--a1-rotation", action="store_true",
+                   help="store A1 for a quarter of the sensor columns (4x smaller, slower)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
     return p.parse_args()
@@ -163,8 +165,13 @@ def stage_model(geom, info, batch, weights):
     y1 = 4 * batch * r1 * geom.mz           # bytes of Y1 (= Y1')
     pp = 4 * batch * r2 * geom.n_phi        # bytes of P' (= p)
     fv = 4 * batch * pix * geom.mz          # bytes of f
-    spmm1 = dict(flop=2 * nnz1 * geom.mz * batch,
-                 bytes=nnz1 * (vb + 4) + 4 * (r1 + 1) + fv + y1)
+    if info.get("a1_rot"):  # a quarter of A1 (and of A1^T) is stored; the rest by rotation
+        a1b = nnz1 // 4 * (vb + 4) + 4 * (r1 // 4 + 1)
+        a1tb = nnz1 // 4 * (vb + 4) + 4 * (pix + 1)
+    else:
+        a1b = nnz1 * (vb + 4) + 4 * (r1 + 1)
+        a1tb = nnz1 * (vb + 4) + 4 * (pix + 1)
+    spmm1 = dict(flop=2 * nnz1 * geom.mz * batch, bytes=a1b + fv + y1)
     if info.get("a2_taps"):  # A2 held by the taps of T: key + value per tap, sub-row pointers
         sub = 4 * (geom.n_ell * (2 * geom.mz - 1) + 1)
         a2b = a2tb = info["n_taps"] * (vb + 4) + sub
@@ -173,7 +180,7 @@ def stage_model(geom, info, batch, weights):
         a2tb = nnz2 * (vb + 4) + 4 * (c1 + 1)
     spmm2 = dict(flop=2 * nnz2 * geom.n_phi * batch, bytes=a2b + y1 + pp)
     spmm2t = dict(flop=spmm2["flop"], bytes=a2tb + pp + y1)
-    spmm1t = dict(flop=spmm1["flop"], bytes=nnz1 * (vb + 4) + 4 * (pix + 1) + y1 + fv)
+    spmm1t = dict(flop=spmm1["flop"], bytes=a1tb + y1 + fv)
     p1 = dict(flop=0, bytes=2 * y1)
     p2 = dict(flop=0, bytes=2 * pp)
     return {"fwd": [("spmm1", spmm1), ("permute1", p1), ("spmm2", spmm2), ("permute2", p2)],
@@ -314,7 +321,8 @@ def run_ours(args):
     build.build()
     pk = peaks()
     sz = I.sizes(args.workload)
-    geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only)
+    geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only,
+                               a1_rotation=args.a1_rotation)
     B = args.batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -432,6 +440,8 @@ def run_ours(args):
                                       "nnz1": plan.info["nnz1"], "nnz2": plan.info["nnz2"],
                                       "a2_form": (f"Toeplitz taps ({plan.info['n_taps']} taps of T)"
                                                   if plan.info["a2_taps"] else "CSR"),
+                                      "a1_form": ("CSR of the first n_phi/4 columns, the rest "
+                                                  "by rotation" if plan.info["a1_rot"] else "CSR"),
                                       "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3)}),
            "roofline": roof, "hbm": hbm, "stages": stages, "clocks": clk, "e2e": e2e,
            "gpu_launches": launches}

@@ -48,6 +48,12 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
 /* Plan flags. */
 #define SRT_KEEP_F64 0x1 /* keep FP64 copies of A1/A2 entries for srt_plan_export */
 #define SRT_CSR_ONLY 0x2 /* store A2, A2^T as CSR even when the taps would serve   */
+/* SRT_A1_ROTATION: with n_phi a multiple of 4 (and ms < 4096), store A1 and
+ * A1^T for the first n_phi/4 sensor columns only: column j + n_phi/4 sees the
+ * pixel grid turned by 90 degrees, A1[(j + n_phi/4, l), rot(p)] = A1[(j, l), p]
+ * with rot(ix, iy) = (ms-1-iy, ix).  A1's memory drops 4x; the A1 product is
+ * ~3% and the A1^T product ~11% slower at 256^3 (srt_plan_info_t.a1_rot). */
+#define SRT_A1_ROTATION 0x8
 /* When the rings sit at the slab centres (n_zs = mz over the volume height),
  * A2[(h,m),(l,k)] = T[m, k-h, l] for a master tensor T, and the plan applies A2
  * and A2^T from T's taps without storing them (srt_plan_info_t.a2_taps = 1),
@@ -91,6 +97,9 @@ typedef struct srt_plan_info_t {
   int32_t weight_dtype;
   int32_t a2_taps;            /* 1: A2, A2^T applied from Toeplitz taps       */
   int64_t n_taps;             /* taps of the master tensor T (0 for CSR A2)   */
+  int32_t a1_rot;             /* 1: only the first n_phi/4 columns of A1 are  */
+                              /*    stored; the rest follow by rotation       */
+  int32_t reserved;
 } srt_plan_info_t;
 
 /*

@@ -16,6 +16,7 @@ SRT_ERR_WORKSPACE, SRT_ERR_TIMEOUT, SRT_ERR_NOT_READY = 5, 6, 7
 SRT_FP32, SRT_BF16 = 0, 1
 SRT_KEEP_F64 = 1
 SRT_CSR_ONLY = 2
+SRT_A1_ROTATION = 8
 SRT_NOALLOC_WORKSPACE_BYTES = 32 << 20
 
 
@@ -37,6 +38,7 @@ class SrtPlanInfo(ctypes.Structure):
         ("dropped1", ctypes.c_int64), ("dropped2", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64), ("weight_dtype", ctypes.c_int32),
         ("a2_taps", ctypes.c_int32), ("n_taps", ctypes.c_int64),
+        ("a1_rot", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 

@@ -10,7 +10,10 @@
 //   P2     p[b][j][(h,m)]   <- P'[(h,m)][b][j]       (Alg. 1 final reshape)
 // Adjoint (Alg. 2): P2^-1, A2^T, P1^-1, A1^T with the transposed matrices.
 #include <math.h>
+#include <algorithm>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -78,12 +81,16 @@ struct HostSink {
   cudaEvent_t ev[kHostChunks] = {};
 };
 
-// Rows [r0, r0 + n) of A as a matrix of its own (row pointers stay absolute).
-SrtCsr rows_view(const SrtCsr& A, int64_t r0, int64_t n) {
-  SrtCsr v = A;
-  v.rows = (int32_t)n;
-  v.rowptr = A.rowptr + r0;
-  return v;
+// How the A1 products reach the rows the plan did not store (SrtRot).
+SrtRot a1_rot(const srt_plan_s* p, int mode) {
+  SrtRot r;
+  if (p->a1_rot) {
+    r.mode = mode;
+    r.ms = p->g.ms;
+    r.n_ell = p->g.n_ell;
+    r.q = p->g.n_phi / 4;
+  }
+  return r;
 }
 
 // Copy `height` rows of `width_elems` floats, `pitch_elems` apart, from the
@@ -111,7 +118,7 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   // Y1[b][j][l][k] = A1 F_b (CRT in the first plane, all slabs at once)
   // rows (j, l) visited radius-chunk-major across sensor columns (L2 reuse of F)
   SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B, st,
-                   g.n_phi, g.n_ell));
+                   g.n_phi, g.n_ell, 1, 0, r1, a1_rot(p, 1)));
   if (!hs) mark(p, 0, 1, st);
   SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
   if (!hs) mark(p, 0, 2, st);
@@ -127,8 +134,8 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
       SRT_TRY(srt_taps_apply(p, false, ra, rn, h1 - h0, g.n_ell, 4, w1, nb, w0 + ra * nb, nb,
                              (int)nb, st));
     else
-      SRT_TRY(srt_spmm(rows_view(p->a2, ra, rn), g.weight_dtype, w1, nb, 0, w0 + ra * nb, nb, 0,
-                       (int)nb, 1, st, h1 - h0, g.n_ell, 4));
+      SRT_TRY(srt_spmm(p->a2, g.weight_dtype, w1, nb, 0, w0 + ra * nb, nb, 0, (int)nb, 1, st,
+                       h1 - h0, g.n_ell, 4, ra, rn));
     if (!hs) mark(p, 0, 3, st);
     SRT_TRY(srt_transpose(w0 + ra * nb, nb, g.n_phi, out + ra, r2, (int64_t)g.n_phi * r2,
                           (int)rn, g.n_phi, B, st));
@@ -167,8 +174,8 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   for (int c = 0; c < nc; ++c) {
     const int x0 = (int)((int64_t)g.ms * c / nc), x1 = (int)((int64_t)g.ms * (c + 1) / nc);
     const int64_t ra = (int64_t)x0 * g.ms, rn = (int64_t)(x1 - x0) * g.ms;
-    SRT_TRY(srt_spmm(rows_view(p->a1t, ra, rn), g.weight_dtype, f1, g.mz, r1 * g.mz,
-                     f + ra * g.mz, g.mz, pix * g.mz, g.mz, B, st, x1 - x0, g.ms, 4));
+    SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f + ra * g.mz, g.mz,
+                     pix * g.mz, g.mz, B, st, x1 - x0, g.ms, 4, ra, rn, a1_rot(p, 2)));
     if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra * g.mz, f + ra * g.mz, rn * g.mz, pix * g.mz, B));
   }
   if (hs) return SRT_OK;
@@ -234,9 +241,9 @@ int srt_plan(const srt_geometry* g, void* stream, srt_plan_t* out) {
 
 int srt_plan_info(srt_plan_t p, srt_plan_info_t* o) {
   if (!p || !o) return SRT_ERR_ARG;
-  o->rows1 = p->a1.rows;
+  o->rows1 = (int64_t)p->g.n_phi * p->g.n_ell;
   o->cols1 = p->a1.cols;
-  o->nnz1 = p->a1.nnz;
+  o->nnz1 = p->nnz1;
   o->rows2 = p->a2.rows;
   o->cols2 = p->a2.cols;
   o->nnz2 = p->a2.nnz;
@@ -246,6 +253,8 @@ int srt_plan_info(srt_plan_t p, srt_plan_info_t* o) {
   o->weight_dtype = p->g.weight_dtype;
   o->a2_taps = p->toeplitz;
   o->n_taps = p->toeplitz ? p->tm.nnz : 0;
+  o->a1_rot = p->a1_rot;
+  o->reserved = 0;
   return SRT_OK;
 }
 
@@ -369,12 +378,94 @@ int export_csr(const SrtCsr* m, int32_t* rowptr, int32_t* col, float* val32, dou
   return SRT_OK;
 }
 
+// Full A1 (transpose = false) or A1^T from the stored quarter of A1: row
+// (j, l) is stored row (j mod q, l) with its pixels turned j / q quarter
+// turns, columns sorted; the transpose is formed on the host by a stable
+// counting sort (rows by increasing source row, as on the device).
+int export_a1_rot(const srt_plan_s* p, bool transpose, int32_t* rowptr, int32_t* col,
+                  float* val32, double* val64) {
+  const SrtCsr& m = p->a1;
+  const srt_geometry& g = p->g;
+  if (val64 && !m.v64) return SRT_ERR_ARG;
+  const int q = g.n_phi / 4, ms = g.ms, ne = g.n_ell;
+  const int64_t ns = m.nnz, rows = (int64_t)g.n_phi * ne, pix = (int64_t)ms * ms;
+  std::vector<int32_t> rp(m.rows + 1), cl(ns);
+  std::vector<float> v(ns);
+  std::vector<double> v64(val64 ? ns : 0);
+  SRT_CUDA_TRY(cudaMemcpy(rp.data(), m.rowptr, rp.size() * 4, cudaMemcpyDeviceToHost));
+  if (ns) {
+    SRT_CUDA_TRY(cudaMemcpy(cl.data(), m.col, ns * 4, cudaMemcpyDeviceToHost));
+    if (m.v32) {
+      SRT_CUDA_TRY(cudaMemcpy(v.data(), m.v32, ns * 4, cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<uint16_t> h(ns);
+      SRT_CUDA_TRY(cudaMemcpy(h.data(), m.v16, ns * 2, cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < ns; ++i) {
+        const uint32_t u = ((uint32_t)h[i]) << 16;
+        memcpy(&v[i], &u, 4);
+      }
+    }
+    if (val64) SRT_CUDA_TRY(cudaMemcpy(v64.data(), m.v64, ns * 8, cudaMemcpyDeviceToHost));
+  }
+  auto turn = [ms](int pp, int s) {
+    const int ix = pp / ms, iy = pp - ix * ms;
+    switch (s & 3) {
+      case 0: return pp;
+      case 1: return (ms - 1 - iy) * ms + ix;
+      case 2: return (ms - 1 - ix) * ms + (ms - 1 - iy);
+      default: return iy * ms + (ms - 1 - ix);
+    }
+  };
+  // full A1, rows sorted by column
+  std::vector<int32_t> frp(rows + 1), fcl(4 * ns);
+  std::vector<float> fv(4 * ns);
+  std::vector<double> f64(val64 ? 4 * ns : 0);
+  std::vector<std::pair<int32_t, int64_t>> tmp;
+  int64_t at = 0;
+  for (int64_t r = 0; r < rows; ++r) {
+    frp[r] = (int32_t)at;
+    const int j = (int)(r / ne), l = (int)(r % ne), s = j / q;
+    const int64_t sr = (int64_t)(j % q) * ne + l;
+    tmp.clear();
+    for (int64_t e = rp[sr]; e < rp[sr + 1]; ++e) tmp.emplace_back(turn(cl[e], s), e);
+    std::sort(tmp.begin(), tmp.end());
+    for (auto& t : tmp) {
+      fcl[at] = t.first;
+      fv[at] = v[t.second];
+      if (val64) f64[at] = v64[t.second];
+      ++at;
+    }
+  }
+  frp[rows] = (int32_t)at;
+  if (!transpose) {
+    memcpy(rowptr, frp.data(), frp.size() * 4);
+    memcpy(col, fcl.data(), at * 4);
+    if (val32) memcpy(val32, fv.data(), at * 4);
+    if (val64) memcpy(val64, f64.data(), at * 8);
+    return SRT_OK;
+  }
+  std::vector<int64_t> cnt(pix + 1, 0);
+  for (int64_t e = 0; e < at; ++e) ++cnt[fcl[e] + 1];
+  for (int64_t i = 0; i < pix; ++i) cnt[i + 1] += cnt[i];
+  for (int64_t i = 0; i <= pix; ++i) rowptr[i] = (int32_t)cnt[i];
+  for (int64_t r = 0; r < rows; ++r)
+    for (int64_t e = frp[r]; e < frp[r + 1]; ++e) {
+      const int64_t d = cnt[fcl[e]]++;
+      col[d] = (int32_t)r;
+      if (val32) val32[d] = fv[e];
+      if (val64) val64[d] = f64[e];
+    }
+  return SRT_OK;
+}
+
 }  // namespace
 
 int srt_plan_export(srt_plan_t p, int32_t which, int32_t* rowptr, int32_t* col, float* val32,
                     double* val64) {
   if (!p || !rowptr || !col) return SRT_ERR_ARG;
   if (which < 1 || which > 4) return SRT_ERR_ARG;
+  if ((which == 1 || which == 3) && p->a1_rot)
+    return export_a1_rot(p, which == 3, rowptr, col, val32, val64);
   if (which == 1 || which == 3 || !p->toeplitz)
     return export_csr(which == 1 ? &p->a1 : which == 2 ? &p->a2 : which == 3 ? &p->a1t : &p->a2t,
                       rowptr, col, val32, val64);

@@ -29,6 +29,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 struct GeomDev {
   int ms, mz, n_phi, n_zs, n_ell;
+  int nj;  // sensor columns whose A1 rows are assembled (the first nj of n_phi)
   double dxy, dz, radius, phi0, zs_lo, zs_hi, ell_lo, ell_hi;
   double hx, hz, dl, thr1, thr2;
 };
@@ -38,6 +39,7 @@ GeomDev make_geom(const srt_geometry& g) {
   G.ms = g.ms;
   G.mz = g.mz;
   G.n_phi = g.n_phi;
+  G.nj = g.n_phi;
   G.n_zs = g.n_zs;
   G.n_ell = g.n_ell;
   G.dxy = g.dxy;
@@ -404,7 +406,7 @@ namespace {
 template <bool A1>
 int assemble_one(const GeomDev& G, int wdt, SrtCsr* m, int64_t* dropped, int64_t* bytes,
                  cudaStream_t st) {
-  const int rows = A1 ? G.n_phi * G.n_ell : G.n_zs * G.n_ell;
+  const int rows = A1 ? G.nj * G.n_ell : G.n_zs * G.n_ell;
   const int cols = A1 ? G.ms * G.ms : G.n_ell * G.mz;
   m->rows = rows;
   m->cols = cols;
@@ -513,7 +515,18 @@ int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
   const GeomDev G = make_geom(plan->g);
   const bool keep = (plan->g.flags & SRT_KEEP_F64) != 0;
   const int wdt = plan->g.weight_dtype;
-  SRT_TRY(assemble_one<true>(G, wdt, &plan->a1, &plan->dropped1, &plan->bytes, st));
+  // A1 by rotation: with n_phi a multiple of 4, column j + n_phi/4 sees the
+  // pixel grid turned by 90 degrees about the axis, so the rows of the first
+  // n_phi/4 columns determine all of A1 (and A1^T)
+  GeomDev G1 = G;
+  if ((plan->g.flags & SRT_A1_ROTATION) && plan->g.n_phi % 4 == 0 && plan->g.ms < 4096) {
+    G1.nj = plan->g.n_phi / 4;
+    plan->a1_rot = 1;
+  }
+  SRT_TRY(assemble_one<true>(G1, wdt, &plan->a1, &plan->dropped1, &plan->bytes, st));
+  const int64_t copies = plan->a1_rot ? 4 : 1;
+  plan->nnz1 = plan->a1.nnz * copies;
+  plan->dropped1 *= copies;
   if (toeplitz_applies(plan->g)) {
     // master tensor: one ring at z = 0 over 2 mz - 1 slabs centred on it;
     // A2 and A2^T are applied from its taps and never stored as matrices

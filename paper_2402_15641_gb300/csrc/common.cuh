@@ -52,6 +52,8 @@ struct srt_plan_s {
   srt_geometry g;
   int device = 0;
   SrtCsr a1, a2, a1t, a2t;  // A1 = A^{1,2}, A2 = A^{3,4} and their transposes
+  int a1_rot = 0;           // a1, a1t hold the first n_phi/4 sensor columns only
+  int64_t nnz1 = 0;         // entries of the full A1
   int toeplitz = 0;         // second product through the Toeplitz taps below
   SrtTaps tf, ta;           // forward / adjoint taps of A2 (a2, a2t then hold no arrays)
   SrtCsr tm;                // master tensor T (rows m, columns l*(2mz-1) + d + mz - 1)
@@ -84,12 +86,22 @@ int srt_taps_apply(const srt_plan_s* plan, bool adjoint, int64_t r0, int64_t row
                    int TG, const float* x, int64_t ldx, float* y, int64_t ldy, int ncols,
                    cudaStream_t stream);
 
-// y[b][r][n] = sum_e A[r, col[e]] * x[b][col[e]][n] for n < ncols.  With G > 0
-// the rows (G groups of R) are visited chunk-major across groups, a block
-// owning TG groups (1, 2, 4 or 8) x 8/TG consecutive rows of each.
+// Output rows of A1 / A1^T served from the stored quarter of A1 (spmm.cu):
+// mode 1 = A1 rows (j, l) from stored rows (j mod q, l), pixels turned;
+// mode 2 = A1^T rows (pixels) from 4 stored rows of the stored transpose.
+struct SrtRot {
+  int mode = 0;           // 0: rows are stored as they are
+  int ms = 0, n_ell = 0;  // pixel grid edge, radius bins
+  int q = 0;              // stored sensor columns (n_phi / 4)
+};
+
+// y[b][r - r0][n] = sum_e A[r, col[e]] * x[b][col[e]][n] for output rows
+// r0 <= r < r0 + rows (rows < 0: to A's end) and n < ncols.  With G > 0 the
+// launch's rows (G groups of R) are visited chunk-major across groups, a
+// block owning TG groups (1, 2, 4 or 8) x 8/TG consecutive rows of each.
 int srt_spmm(const SrtCsr& A, int weight_dtype, const float* x, int64_t ldx, int64_t bsx, float* y,
              int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t stream, int G = 0,
-             int R = 0, int TG = 1);
+             int R = 0, int TG = 1, int64_t r0 = 0, int64_t rows = -1, SrtRot rot = SrtRot());
 
 // out[b*obs + c*old + r] = in[b*ibs + r*ild + c] for r < rows, c < cols.
 int srt_transpose(const float* in, int64_t ild, int64_t ibs, float* out, int64_t old, int64_t obs,

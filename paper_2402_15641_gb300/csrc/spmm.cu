@@ -6,6 +6,16 @@
 // Lanes own consecutive dense columns (float4 when rows are 16-byte aligned);
 // a row's (column, value) pairs are loaded 32 at a time and broadcast with
 // warp shuffles.  Entries are FP32 or BF16; accumulation is FP32.
+//
+// A1 by rotation (SrtRot): with n_phi a multiple of 4, sensor column
+// j + n_phi/4 sees the image turned by 90 degrees about the axis, so
+//   A1[(j + s n_phi/4, l), rot^s(p)] = A1[(j, l), p],
+//   rot(ix, iy) = (ms-1-iy, ix),
+// and only the rows of the first n_phi/4 columns are stored.  Mode 1 (A1):
+// output row (j, l) walks stored row (j mod n_phi/4, l) and gathers pixel
+// rot^s(p).  Mode 2 (A1^T): output row p walks, for s = 0..3, stored row
+// rot^-s(p) of the stored transpose and gathers row (j + s n_phi/4, l): the
+// same terms in the same order (ascending j, then l) as the full transpose.
 #include "common.cuh"
 
 namespace {
@@ -23,9 +33,19 @@ __device__ __forceinline__ float wval<uint16_t>(uint16_t v) {
   return srt_bf16_to_f32(v);
 }
 
-// Vector path: each lane owns 4 consecutive columns of each 128-column chunk;
-// a warp covers CH chunks.  Requires ncols, ldx, ldy multiples of 4 and
-// 16-byte aligned bases.
+// Pixel p = ix*ms + iy turned s quarter turns: rot(ix, iy) = (ms-1-iy, ix).
+// ix = floor(p / ms) as (p * magic) >> 40 with magic = ceil(2^40 / ms), exact
+// for p < 2^24 and ms < 2^16 (the quotient's error stays below 1/ms).
+__device__ __forceinline__ int rot_pixel(int p, int s, int ms, uint64_t magic) {
+  const int ix = (int)(((uint64_t)(uint32_t)p * magic) >> 40), iy = p - ix * ms;
+  switch (s & 3) {
+    case 0: return p;
+    case 1: return (ms - 1 - iy) * ms + ix;
+    case 2: return (ms - 1 - ix) * ms + (ms - 1 - iy);
+    default: return iy * ms + (ms - 1 - ix);
+  }
+}
+
 // Block-to-rows order.  Rows come in G groups of R rows (r = g*R + i).  With
 // G > 0 a block owns a tile of TG groups x 8/TG consecutive i, and
 // consecutive blocks take the same chunk of i in consecutive group tiles
@@ -45,13 +65,42 @@ __device__ __forceinline__ int block_row(int G, int R, int TG) {
   return (g < G && i < R) ? g * R + i : -1;
 }
 
+struct Rows {
+  int rows, r0;    // output rows of this launch, first output row
+  int G, R, TG;    // block order
+  SrtRot rot;
+  uint64_t magic;  // ceil(2^40 / rot.ms)
+};
+
+// Stored row and gathered-row remap of segment s of output row `row`.
+template <int MODE>
+__device__ __forceinline__ int seg_row(const Rows& A, int row, int s) {
+  if (MODE == 1) {
+    const int j = row / A.rot.n_ell, l = row - j * A.rot.n_ell;
+    return (j % A.rot.q) * A.rot.n_ell + l;
+  }
+  if (MODE == 2) return rot_pixel(row, 4 - s, A.rot.ms, A.magic);
+  return row;
+}
+// Gathered row of stored column c in segment s (t: quarter turns of the row).
+template <int MODE>
+__device__ __forceinline__ int seg_col(const Rows& A, int t, int s, int c) {
+  if (MODE == 1) return rot_pixel(c, t, A.rot.ms, A.magic);
+  if (MODE == 2) return c + s * A.rot.q * A.rot.n_ell;
+  return c;
+}
+
+// Rows stored as they are (no rotation).  rowptr is the launch's first row's
+// pointer.  (A single kernel for both cases, with the row bookkeeping behind
+// a struct passed by reference, measured 3% slower.)
 template <typename V, int CH>
-__global__ void __launch_bounds__(256) k_spmm_vec(int rows, const int32_t* __restrict__ rowptr,
-                                                  const int32_t* __restrict__ col,
-                                                  const V* __restrict__ val,
-                                                  const float* __restrict__ x, int64_t ldx,
-                                                  int64_t bsx, float* __restrict__ y, int64_t ldy,
-                                                  int64_t bsy, int ncols, int G, int R, int TG) {
+__global__ void __launch_bounds__(256) k_spmm_plain(int rows, const int32_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col,
+                                                    const V* __restrict__ val,
+                                                    const float* __restrict__ x, int64_t ldx,
+                                                    int64_t bsx, float* __restrict__ y,
+                                                    int64_t ldy, int64_t bsy, int ncols, int G,
+                                                    int R, int TG) {
   const int lane = threadIdx.x & 31;
   const int row = block_row(G, R, TG);
   if (row < 0 || row >= rows) return;
@@ -95,44 +144,120 @@ __global__ void __launch_bounds__(256) k_spmm_vec(int rows, const int32_t* __res
   }
 }
 
+// A1 / A1^T from the stored quarter of A1 (the plain loop with the stored
+// row and the gathered row remapped; scalar parameters only).  MODE 1: row
+// (j, l) of A1 from stored row (j mod q, l), pixels turned j / q times.
+// MODE 2: row p of A1^T from stored rows rot^-s(p), s = 0..3, gathered rows
+// shifted by s q n_ell.  rowptr: the stored matrix's own pointers.
+template <typename V, int CH, int MODE>
+__global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
+                                                  const int32_t* __restrict__ rowptr,
+                                                  const int32_t* __restrict__ col,
+                                                  const V* __restrict__ val,
+                                                  const float* __restrict__ x, int64_t ldx,
+                                                  int64_t bsx, float* __restrict__ y, int64_t ldy,
+                                                  int64_t bsy, int ncols, int G, int R, int TG,
+                                                  int ms, int n_ell, int q, uint64_t magic) {
+  const int lane = threadIdx.x & 31;
+  const int lr = block_row(G, R, TG);
+  if (lr < 0 || lr >= rows) return;
+  const int row = r0 + lr;
+  x += blockIdx.z * bsx;
+  y += blockIdx.z * bsy;
+  const int n0 = blockIdx.y * (128 * CH) + lane * 4;
+  float4 acc[CH];
+#pragma unroll
+  for (int k = 0; k < CH; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  int t = 0, sr = row;
+  if (MODE == 1) {
+    const int j = row / n_ell, l = row - j * n_ell;
+    t = j / q;
+    sr = (j - t * q) * n_ell + l;
+  }
+#pragma unroll 1
+  for (int s = 0; s < (MODE == 2 ? 4 : 1); ++s) {
+    if (MODE == 2) sr = rot_pixel(row, 4 - s, ms, magic);
+    const int off = MODE == 2 ? s * q * n_ell : 0;
+    const int e0 = rowptr[sr], e1 = rowptr[sr + 1];
+    for (int eb = e0; eb < e1; eb += 32) {
+      int c = 0;
+      float v = 0.f;
+      if (eb + lane < e1) {
+        c = col[eb + lane];
+        c = MODE == 1 ? rot_pixel(c, t, ms, magic) : c + off;
+        v = wval<V>(val[eb + lane]);
+      }
+      const int cnt = min(32, e1 - eb);
+      for (int i = 0; i < cnt; ++i) {
+        const int ci = __shfl_sync(FULL, c, i);
+        const float vi = __shfl_sync(FULL, v, i);
+        const float* xr = x + (int64_t)ci * ldx;
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+          const int n = n0 + k * 128;
+          if (n < ncols) {
+            const float4 xv = __ldg(reinterpret_cast<const float4*>(xr + n));
+            acc[k].x = fmaf(vi, xv.x, acc[k].x);
+            acc[k].y = fmaf(vi, xv.y, acc[k].y);
+            acc[k].z = fmaf(vi, xv.z, acc[k].z);
+            acc[k].w = fmaf(vi, xv.w, acc[k].w);
+          }
+        }
+      }
+    }
+  }
+  float* yr = y + (int64_t)lr * ldy;
+#pragma unroll
+  for (int k = 0; k < CH; ++k) {
+    const int n = n0 + k * 128;
+    if (n < ncols) *reinterpret_cast<float4*>(yr + n) = acc[k];
+  }
+}
+
 // Scalar path for any ncols / strides: lane owns columns lane + 32 i.
-template <typename V, int PER>
-__global__ void __launch_bounds__(256) k_spmm_scalar(int rows, const int32_t* __restrict__ rowptr,
+template <typename V, int PER, int MODE>
+__global__ void __launch_bounds__(256) k_spmm_scalar(Rows A, const int32_t* __restrict__ rowptr,
                                                      const int32_t* __restrict__ col,
                                                      const V* __restrict__ val,
                                                      const float* __restrict__ x, int64_t ldx,
                                                      int64_t bsx, float* __restrict__ y,
                                                      int64_t ldy, int64_t bsy, int ncols) {
   const int lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row >= rows) return;
+  const int lr = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (lr >= A.rows) return;
+  const int row = A.r0 + lr;
   x += blockIdx.z * bsx;
   y += blockIdx.z * bsy;
   const int n0 = blockIdx.y * (32 * PER) + lane;
   float acc[PER];
 #pragma unroll
   for (int q = 0; q < PER; ++q) acc[q] = 0.f;
-  const int e0 = rowptr[row], e1 = rowptr[row + 1];
-  for (int eb = e0; eb < e1; eb += 32) {
-    int c = 0;
-    float v = 0.f;
-    if (eb + lane < e1) {
-      c = col[eb + lane];
-      v = wval<V>(val[eb + lane]);
-    }
-    const int cnt = min(32, e1 - eb);
-    for (int i = 0; i < cnt; ++i) {
-      const int ci = __shfl_sync(FULL, c, i);
-      const float vi = __shfl_sync(FULL, v, i);
-      const float* xr = x + (int64_t)ci * ldx;
+  constexpr int NSEG = MODE == 2 ? 4 : 1;
+  const int t = MODE == 1 ? (row / A.rot.n_ell) / A.rot.q : 0;
+  for (int s = 0; s < NSEG; ++s) {
+    const int sr = seg_row<MODE>(A, row, s);
+    const int e0 = rowptr[sr], e1 = rowptr[sr + 1];
+    for (int eb = e0; eb < e1; eb += 32) {
+      int c = 0;
+      float v = 0.f;
+      if (eb + lane < e1) {
+        c = seg_col<MODE>(A, t, s, col[eb + lane]);
+        v = wval<V>(val[eb + lane]);
+      }
+      const int cnt = min(32, e1 - eb);
+      for (int i = 0; i < cnt; ++i) {
+        const int ci = __shfl_sync(FULL, c, i);
+        const float vi = __shfl_sync(FULL, v, i);
+        const float* xr = x + (int64_t)ci * ldx;
 #pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int n = n0 + q * 32;
-        if (n < ncols) acc[q] = fmaf(vi, __ldg(xr + n), acc[q]);
+        for (int q = 0; q < PER; ++q) {
+          const int n = n0 + q * 32;
+          if (n < ncols) acc[q] = fmaf(vi, __ldg(xr + n), acc[q]);
+        }
       }
     }
   }
-  float* yr = y + (int64_t)row * ldy;
+  float* yr = y + (int64_t)lr * ldy;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int n = n0 + q * 32;
@@ -140,53 +265,79 @@ __global__ void __launch_bounds__(256) k_spmm_scalar(int rows, const int32_t* __
   }
 }
 
-template <typename V>
-int launch(const SrtCsr& A, const V* val, const float* x, int64_t ldx, int64_t bsx, float* y,
-           int64_t ldy, int64_t bsy, int ncols, int batch, int G, int R, int TG, cudaStream_t st) {
-  const int rows_per_block = 8;
+template <typename V, int MODE>
+int launch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t ldx, int64_t bsx,
+           float* y, int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t st) {
   dim3 block(256);
   const bool vec = (ncols % 4 == 0) && (ldx % 4 == 0) && (ldy % 4 == 0) && (bsx % 4 == 0) &&
                    (bsy % 4 == 0) && ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0);
-  if (G > 0 && (int64_t)G * R != A.rows) G = 0;
-  if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 1;
-  const int gx = G > 0 ? ((G + TG - 1) / TG) * ((R + 8 / TG - 1) / (8 / TG))
-                       : (A.rows + rows_per_block - 1) / rows_per_block;
-  if (vec) {
+  const int gx = W.G > 0 ? ((W.G + W.TG - 1) / W.TG) * ((W.R + 8 / W.TG - 1) / (8 / W.TG))
+                         : (W.rows + 7) / 8;
+  if (vec && MODE == 0) {
+    const int32_t* rp = A.rowptr + W.r0;
     const int chunks = (ncols + 127) / 128;
-    if (chunks >= 4) {
-      dim3 grid(gx, (ncols + 511) / 512, batch);
-      k_spmm_vec<V, 4><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                               bsy, ncols, G, R, TG);
-    } else if (chunks == 3) {
-      dim3 grid(gx, 1, batch);
-      k_spmm_vec<V, 3><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                               bsy, ncols, G, R, TG);
-    } else if (chunks == 2) {
-      dim3 grid(gx, 1, batch);
-      k_spmm_vec<V, 2><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                               bsy, ncols, G, R, TG);
-    } else {
-      dim3 grid(gx, 1, batch);
-      k_spmm_vec<V, 1><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                               bsy, ncols, G, R, TG);
+    const int CH = chunks >= 4 ? 4 : chunks;
+    dim3 grid(gx, CH == 4 ? (ncols + 511) / 512 : 1, batch);
+    switch (CH) {
+      case 4: k_spmm_plain<V, 4><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG); break;
+      case 3: k_spmm_plain<V, 3><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG); break;
+      case 2: k_spmm_plain<V, 2><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG); break;
+      default: k_spmm_plain<V, 1><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG); break;
     }
+  } else if (vec) {
+    const int chunks = (ncols + 127) / 128;
+    const int CH = chunks >= 4 ? 4 : chunks;
+    dim3 grid(gx, CH == 4 ? (ncols + 511) / 512 : 1, batch);
+    const SrtRot& r = W.rot;
+#define SRT_ROT_LAUNCH(C)                                                                     \
+  k_spmm_rot<V, C, MODE><<<grid, block, 0, st>>>(W.rows, W.r0, A.rowptr, A.col, val, x, ldx, \
+                                                 bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG,    \
+                                                 r.ms, r.n_ell, r.q, W.magic)
+    switch (CH) {
+      case 4: SRT_ROT_LAUNCH(4); break;
+      case 3: SRT_ROT_LAUNCH(3); break;
+      case 2: SRT_ROT_LAUNCH(2); break;
+      default: SRT_ROT_LAUNCH(1); break;
+    }
+#undef SRT_ROT_LAUNCH
   } else {
-    dim3 grid((A.rows + rows_per_block - 1) / rows_per_block, (ncols + 127) / 128, batch);
-    k_spmm_scalar<V, 4><<<grid, block, 0, st>>>(A.rows, A.rowptr, A.col, val, x, ldx, bsx, y, ldy,
-                                                bsy, ncols);
+    dim3 grid((W.rows + 7) / 8, (ncols + 127) / 128, batch);
+    k_spmm_scalar<V, 4, MODE><<<grid, block, 0, st>>>(W, A.rowptr, A.col, val, x, ldx, bsx, y,
+                                                      ldy, bsy, ncols);
   }
   SRT_CUDA_TRY(cudaGetLastError());
   return SRT_OK;
 }
 
+template <typename V>
+int dispatch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t ldx,
+             int64_t bsx, float* y, int64_t ldy, int64_t bsy, int ncols, int batch,
+             cudaStream_t st) {
+  switch (W.rot.mode) {
+    case 1: return launch<V, 1>(A, val, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
+    case 2: return launch<V, 2>(A, val, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
+    default: return launch<V, 0>(A, val, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
+  }
+}
 
 }  // namespace
 
 int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx, float* y,
              int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t st, int G, int R,
-             int TG) {
-  if (wdt == SRT_BF16)
-    return launch<uint16_t>(A, A.v16, x, ldx, bsx, y, ldy, bsy, ncols, batch, G, R, TG, st);
-  return launch<float>(A, A.v32, x, ldx, bsx, y, ldy, bsy, ncols, batch, G, R, TG, st);
+             int TG, int64_t r0, int64_t rows, SrtRot rot) {
+  if (rows < 0) rows = A.rows - r0;
+  if (rows <= 0) return SRT_OK;
+  if (rows > 0x7fffffff || r0 + rows > 0x7fffffff) return SRT_ERR_ARG;
+  uint64_t magic = 0;
+  if (rot.mode != 0) {
+    if (rot.q <= 0 || rot.ms <= 0 || rot.ms >= (1 << 16) || rot.n_ell <= 0 ||
+        (int64_t)rot.ms * rot.ms >= (1 << 24))
+      return SRT_ERR_ARG;
+    magic = ((1ull << 40) + rot.ms - 1) / rot.ms;
+  }
+  if (G > 0 && (int64_t)G * R != rows) G = 0;
+  if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 1;
+  const Rows W{(int)rows, (int)r0, G, R, TG, rot, magic};
+  if (wdt == SRT_BF16) return dispatch<uint16_t>(A, A.v16, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
+  return dispatch<float>(A, A.v32, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
 }
-

@@ -40,11 +40,12 @@ class Geometry:
     weight_dtype: str = "fp32"  # "fp32" | "bf16"
     keep_f64: bool = False
     csr_only: bool = False
+    a1_rotation: bool = False
 
     @staticmethod
     def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, **options) -> "Geometry":
         """Default readings, computed by the library (srt_geometry_default);
-        options set weight_dtype / keep_f64 / csr_only."""
+        options set weight_dtype / keep_f64 / csr_only / a1_rotation."""
         g = L.SrtGeometry()
         check(L.lib().srt_geometry_default(ctypes.byref(g), ms, mz, dxy, dz, radius, n_phi, n_zs,
                                            n_ell), "srt_geometry_default")
@@ -65,7 +66,8 @@ class Geometry:
                              self.phi0, self.n_zs, self.zs_lo, self.zs_hi, self.n_ell,
                              self.ell_lo, self.ell_hi, wd,
                              (L.SRT_KEEP_F64 if self.keep_f64 else 0)
-                             | (L.SRT_CSR_ONLY if self.csr_only else 0))
+                             | (L.SRT_CSR_ONLY if self.csr_only else 0)
+                             | (L.SRT_A1_ROTATION if self.a1_rotation else 0))
 
     @property
     def f_shape(self):
@@ -107,7 +109,7 @@ class Plan:
         self._ws = {}
         info = L.SrtPlanInfo()
         check(self._lib.srt_plan_info(self._h, ctypes.byref(info)), "srt_plan_info")
-        self.info = {k: getattr(info, k) for k, _ in L.SrtPlanInfo._fields_}
+        self.info = {k: getattr(info, k) for k, _ in L.SrtPlanInfo._fields_ if k != "reserved"}
 
     # -------------------------------------------------------------- memory
     def workspace_bytes(self, batch: int = 1) -> int:

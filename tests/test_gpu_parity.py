@@ -195,13 +195,15 @@ def test_batch16_bitwise_per_volume(srt, orc, wdt):
     assert rel_l2(to_np(ab[7]), orc.adjoint(o, y[7])) <= tol
 
 
-@pytest.mark.parametrize("sz", [RAGGED[0], RAGGED[3], dict(I.sizes("srt32"))])
-def test_host_calls_chunked_equal_device(srt, orc, sz):
+@pytest.mark.parametrize("sz,rot", [(RAGGED[0], False), (RAGGED[3], False),
+                                    (dict(I.sizes("srt32")), False), (dict(I.sizes("srt32")), True)])
+def test_host_calls_chunked_equal_device(srt, orc, sz, rot):
     """The host-buffer calls compute the last product in row ranges and copy
     each back while the next is computed: results equal the device path
-    bitwise, also when there are fewer rings or pixel columns than chunks."""
+    bitwise, also when there are fewer rings or pixel columns than chunks and
+    when A1^T comes from the stored quarter of A1."""
     import torch
-    g, _ = geom_pair(orc, **sz)
+    g, _ = geom_pair(orc, a1_rotation=rot, **sz)
     plan = srt.Plan(g)
     rng = np.random.default_rng(13)
     f = torch.from_numpy(rng.uniform(0, 1, (2, *g.f_shape)).astype(np.float32)).pin_memory()
@@ -317,3 +319,43 @@ def test_plan_info_and_timing(srt, orc):
     assert c.info["a2_taps"] == 0 and c.info["n_taps"] == 0
     assert c.launches_per_call(0) == 4 and c.launches_per_call(1) == 4
     torch.cuda.synchronize()
+
+
+ROT = [dict(I.sizes("srt32")),
+       dict(ms=7, mz=5, dxy=0.5, dz=0.37, radius=6.0, n_phi=8, n_zs=3, n_ell=13, phi0=0.2),
+       dict(ms=12, mz=9, dxy=0.4, dz=0.3, radius=6.0, n_phi=12, n_zs=5, n_ell=21, zs=(-1.0, 1.2))]
+
+
+@pytest.mark.parametrize("sz", ROT)
+@pytest.mark.parametrize("wdt", ["fp32", "bf16"])
+def test_a1_by_rotation(srt, orc, sz, wdt):
+    """With SRT_A1_ROTATION and n_phi a multiple of 4 the plan stores A1 for
+    the first n_phi/4 sensor columns only; column j + n_phi/4 sees the pixel
+    grid turned by 90 degrees.  The full A1 and A1^T it stands for (exported) have the pattern
+    of the directly assembled ones and their FP64 entries to rounding, and the
+    transforms match the fully stored plan and the oracle (odd ms, a phase
+    phi0, rings off the slab centres, BF16, batch 2)."""
+    g, o = geom_pair(orc, weight_dtype=wdt, keep_f64=True, **sz)
+    a = srt.Plan(g.with_(a1_rotation=True))
+    b = srt.Plan(g)
+    assert a.info["a1_rot"] == 1 and b.info["a1_rot"] == 0
+    assert a.info["rows1"] == b.info["rows1"] and a.info["nnz1"] == b.info["nnz1"]
+    assert a.info["device_bytes"] < b.info["device_bytes"]
+    for which in (1, 3):
+        ra, ca, va, da = a.export(which, f64=True)
+        rb, cb, vb, db = b.export(which, f64=True)
+        np.testing.assert_array_equal(ra, rb)
+        np.testing.assert_array_equal(ca, cb)
+        np.testing.assert_allclose(da, db, rtol=1e-12, atol=1e-12 * sz["dxy"])
+        assert rel_l2(va, vb) <= 1e-6
+    rng = np.random.default_rng(14)
+    f = to_dev(rng.uniform(0, 1, (2, *g.f_shape)))
+    y = to_dev(rng.standard_normal((2, *g.p_shape)))
+    assert rel_l2(to_np(a.forward(f)), to_np(b.forward(f))) <= 1e-5
+    assert rel_l2(to_np(a.adjoint(y)), to_np(b.adjoint(y))) <= 1e-5
+    tol = FP32_TOL if wdt == "fp32" else BF16_TOL
+    assert rel_l2(to_np(a.forward(f))[1], orc.forward(o, to_np(f)[1])) <= tol
+    assert rel_l2(to_np(a.adjoint(y))[0], orc.adjoint(o, to_np(y)[0])) <= tol
+    lhs, rhs = srt.dot_f64(a.forward(f), y), srt.dot_f64(f, a.adjoint(y))
+    nrm = math.sqrt(srt.dot_f64(a.forward(f), a.forward(f)) * srt.dot_f64(y, y))
+    assert abs(lhs - rhs) / nrm <= ADJ_TOL
