@@ -111,7 +111,10 @@ def _plan_status(L, **kw):
 @pytest.mark.parametrize("kw", [dict(ms=0), dict(mz=-1), dict(n_phi=0), dict(n_ell=0),
                                 dict(dxy=0.0), dict(dz=-1.0), dict(radius=2.0),
                                 dict(ell_lo=0.0), dict(ell_lo=-1.0), dict(ell_hi=1.0),
-                                dict(zs_hi=-10.0), dict(weight_dtype=7), dict(phi0=float("nan"))])
+                                dict(zs_hi=-10.0), dict(weight_dtype=7), dict(phi0=float("nan")),
+                                # index ranges beyond int32: pixels, A1 rows, (radius, slab) cells
+                                dict(ms=46341, radius=1e6), dict(n_phi=1 << 20, n_ell=1 << 12),
+                                dict(mz=1 << 20, n_ell=1 << 12)])
 def test_invalid_geometry_rejected_before_device_work(L, kw):
     s, h = _plan_status(L, **kw)
     assert s == L.SRT_ERR_GEOMETRY
