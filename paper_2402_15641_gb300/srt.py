@@ -124,6 +124,9 @@ class Plan:
         return n.value
 
     def workspace(self, batch: int = 1, host: bool = False) -> torch.Tensor:
+        """The plan's cached workspace for `batch` (shared by every call that
+        passes no workspace: calls that may overlap on the device, e.g. on
+        different streams or threads, need workspaces of their own)."""
         key = (batch, host)
         if key not in self._ws:
             nb = self.host_workspace_bytes(batch) if host else self.workspace_bytes(batch)

@@ -359,3 +359,54 @@ def test_a1_by_rotation(srt, orc, sz, wdt):
     lhs, rhs = srt.dot_f64(a.forward(f), y), srt.dot_f64(f, a.adjoint(y))
     nrm = math.sqrt(srt.dot_f64(a.forward(f), a.forward(f)) * srt.dot_f64(y, y))
     assert abs(lhs - rhs) / nrm <= ADJ_TOL
+
+
+def test_concurrent_calls_on_one_plan(srt, orc):
+    """The plan is immutable: forward and adjoint calls on different streams
+    (each with its own workspace), and from two host threads, overlap on the
+    device and give bitwise the results of sequential calls."""
+    import threading
+    import torch
+    g, _ = geom_pair(orc, **dict(I.sizes("srt32")))
+    plan = srt.Plan(g)
+    rng = np.random.default_rng(15)
+    fs = [to_dev(rng.uniform(0, 1, g.f_shape)) for _ in range(4)]
+    ys = [to_dev(rng.standard_normal(g.p_shape)) for _ in range(4)]
+    want_p = [plan.forward(f) for f in fs]
+    want_a = [plan.adjoint(y) for y in ys]
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    nb = plan.workspace_bytes(1)
+    wss = [torch.empty(nb, dtype=torch.uint8, device="cuda") for _ in range(4)]
+    outs_p = [torch.empty_like(w) for w in want_p]
+    outs_a = [torch.empty_like(w) for w in want_a]
+    for rep in range(3):
+        for i, st in enumerate(streams):
+            with torch.cuda.stream(st):
+                plan.forward(fs[i], out=outs_p[i], workspace=wss[i], stream=st)
+                plan.adjoint(ys[i], out=outs_a[i], workspace=wss[i], stream=st)
+        torch.cuda.synchronize()
+        for i in range(4):
+            assert torch.equal(outs_p[i], want_p[i]) and torch.equal(outs_a[i], want_a[i])
+    errors = []
+
+    def worker(i):
+        try:
+            st = torch.cuda.Stream()
+            ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            with torch.cuda.stream(st):
+                for _ in range(5):
+                    p = torch.empty_like(want_p[i])
+                    plan.forward(fs[i], out=p, workspace=ws, stream=st)
+                    st.synchronize()
+                    if not torch.equal(p, want_p[i]):
+                        errors.append(i)
+        except Exception as exc:  # reported below
+            errors.append(repr(exc))
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
