@@ -46,15 +46,17 @@ class OracleGeometry:
     n_ell: int
     ell_lo: float
     ell_hi: float
+    rho_linear: bool = False  # intermediate piecewise linear in rho (else constant on bins)
 
     @staticmethod
-    def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, phi0=0.0):
+    def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, phi0=0.0, rho_linear=False):
         """Default readings: rings at cell centres of the volume height and a
         radius grid covering [R - r_xy, R + r_xy], r_xy = ms*dxy/sqrt(2)."""
         h = mz * dz
         rxy = ms * dxy / math.sqrt(2.0)
         return OracleGeometry(ms, mz, float(dxy), float(dz), float(radius), n_phi, float(phi0),
-                              n_zs, -0.5 * h, 0.5 * h, n_ell, radius - rxy, radius + rxy)
+                              n_zs, -0.5 * h, 0.5 * h, n_ell, radius - rxy, radius + rxy,
+                              bool(rho_linear))
 
     @property
     def n_vox(self):
@@ -79,12 +81,13 @@ class _Geom(ctypes.Structure):
         ("n_phi", ctypes.c_int32), ("phi0", ctypes.c_double),
         ("n_zs", ctypes.c_int32), ("zs_lo", ctypes.c_double), ("zs_hi", ctypes.c_double),
         ("n_ell", ctypes.c_int32), ("ell_lo", ctypes.c_double), ("ell_hi", ctypes.c_double),
+        ("rho_linear", ctypes.c_int32),
     ]
 
 
 def _cg(g: OracleGeometry) -> _Geom:
     return _Geom(g.ms, g.mz, g.dxy, g.dz, g.radius, g.n_phi, g.phi0, g.n_zs, g.zs_lo, g.zs_hi,
-                 g.n_ell, g.ell_lo, g.ell_hi)
+                 g.n_ell, g.ell_lo, g.ell_hi, int(g.rho_linear))
 
 
 def build(force: bool = False) -> str:
@@ -233,8 +236,10 @@ def circle_arcs(g: OracleGeometry, j: int, l: int) -> dict:
 
 
 def semicircle_arcs(g: OracleGeometry, h: int, m: int) -> dict:
-    """(z, rho) semicircle (ring h, radius l_m): {cell l*mz + k: arc length}."""
-    cap = 2 * (g.mz + 1) + 2 * (g.n_ell + 1) + 4
+    """(z, rho) semicircle (ring h, radius l_m): {cell l*mz + k: weight}; the
+    weight is the arc length in the cell (piecewise-constant intermediate) or
+    the node's hat integrated along the arc in the slab (piecewise linear)."""
+    cap = 2 * (2 * (g.mz + 1) + 2 * (g.n_ell + 2) + 4)
     cell = np.zeros(cap, dtype=np.int32)
     ln = np.zeros(cap, dtype=np.float64)
     n = lib().orc_semicircle_arcs(ctypes.byref(_cg(g)), h, m, _iptr(cell), _dptr(ln), cap)

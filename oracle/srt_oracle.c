@@ -35,6 +35,16 @@
  *     [zs_lo, zs_hi]; voxel centres (i - (M-1)/2) * spacing (box centred at 0);
  *   - arc lengths in mm, no normalisation.
  *
+ * Piecewise-linear intermediate (rho_linear = 1; the paper notes that the
+ * algorithms carry over to other bases, naming piecewise-linear ones): f^{1,2}
+ * is interpolated linearly in rho between the bin centres rho_l (the nodes),
+ * held constant from lo to rho_0 and from rho_{n-1} to hi, still piecewise
+ * constant in z.  The t-breakpoints are then the crossings with the radii
+ * lo, rho_0, ..., rho_{n-1}, hi, and a segment between nodes rho_l and
+ * rho_{l+1} gives node l the weight int (rho_{l+1} - rho) ds / dl and node l+1
+ * the weight int (rho - rho_l) ds / dl, with int ds = l_m dt and
+ * int rho ds = l_m^2 (cos t0 - cos t1) along the semicircle rho = l_m sin t.
+ *
  * Layouts: f[ix][iy][iz] (z fastest), p[j][h][m].  All arithmetic is FP64.
  */
 #include <math.h>
@@ -57,6 +67,7 @@ typedef struct {
   double zs_lo, zs_hi;   /* ring heights are cell centres of [lo, hi]      */
   int32_t n_ell;         /* radius bins shared by rho and l                */
   double ell_lo, ell_hi; /* radius grid range                              */
+  int32_t rho_linear;    /* 1: f^{1,2} piecewise linear in rho (see above) */
 } orc_geom;
 
 /* ---------------------------------------------------------------- helpers */
@@ -82,33 +93,40 @@ static double sensor_y(const orc_geom* g, int j) {
   return g->radius * sin(g->phi0 + 2.0 * ORC_PI * j / g->n_phi);
 }
 
-/* Work buffers of one thread. */
+/* Work buffers of one thread: t-breakpoints, a-breakpoints and two cached
+ * in-plane circles (a piecewise-linear segment needs two radii at once). */
 typedef struct {
-  double* tb;   /* t-breakpoints                 */
-  double* ab;   /* a-breakpoints                 */
-  int* cpix;    /* cached circle: pixel index    */
-  double* clen; /* cached circle: arc length     */
-  int cn;       /* cached circle: segment count  */
-  int cl;       /* cached circle: radius bin, -1 */
+  double* tb;      /* t-breakpoints                  */
+  double* ab;      /* a-breakpoints                  */
+  int* cpix[2];    /* cached circle: pixel index     */
+  double* clen[2]; /* cached circle: arc length      */
+  int cn[2];       /* cached circle: segment count   */
+  int cl[2];       /* cached circle: radius index, -1 */
 } orc_ws;
 
 static int ws_init(orc_ws* w, const orc_geom* g) {
-  int nt = 2 * (g->mz + 1) + 2 * (g->n_ell + 1) + 4;
+  int nt = 2 * (g->mz + 1) + 2 * (g->n_ell + 2) + 4;
   int na = 4 * (g->ms + 1) + 4;
   w->tb = (double*)malloc(sizeof(double) * nt);
   w->ab = (double*)malloc(sizeof(double) * na);
-  w->cpix = (int*)malloc(sizeof(int) * na);
-  w->clen = (double*)malloc(sizeof(double) * na);
-  w->cn = 0;
-  w->cl = -1;
-  return (w->tb && w->ab && w->cpix && w->clen) ? 0 : -1;
+  int ok = w->tb && w->ab;
+  for (int c = 0; c < 2; ++c) {
+    w->cpix[c] = (int*)malloc(sizeof(int) * na);
+    w->clen[c] = (double*)malloc(sizeof(double) * na);
+    w->cn[c] = 0;
+    w->cl[c] = -1;
+    ok = ok && w->cpix[c] && w->clen[c];
+  }
+  return ok ? 0 : -1;
 }
 
 static void ws_free(orc_ws* w) {
   free(w->tb);
   free(w->ab);
-  free(w->cpix);
-  free(w->clen);
+  for (int c = 0; c < 2; ++c) {
+    free(w->cpix[c]);
+    free(w->clen[c]);
+  }
 }
 
 /* ------------------------------------------------- in-plane circle walk
@@ -171,12 +189,14 @@ static int circle_walk(const orc_geom* g, double sx, double sy, double rho, doub
  * elementary contribution; voxel = (ix*ms + iy)*mz + k.                  */
 typedef void (*emit_fn)(void* ctx, long voxel, double weight);
 
-static void shell_walk_k(const orc_geom* g, orc_ws* w, int j, int h, int m, int k_lo, int k_hi,
-                         emit_fn emit, void* ctx) {
+static int circle_walk(const orc_geom* g, double sx, double sy, double rho, double* ab,
+                       int* pix, double* len);
+
+/* t-breakpoints of the semicircle (z_h + l cos t, l sin t): slab planes and
+ * the radii that bound the intermediate's pieces (bin edges, or for the
+ * piecewise-linear intermediate lo, the bin centres and hi).  Sorted. */
+static int shell_breaks(const orc_geom* g, double ell, double zc, double* tb) {
   const double hz = half_z(g), dl = dell(g);
-  const double ell = ell_centre(g, m), zc = ring_z(g, h);
-  const double sx = sensor_x(g, j), sy = sensor_y(g, j);
-  double* tb = w->tb;
   int n = 0;
   tb[n++] = 0.0;
   tb[n++] = ORC_PI;
@@ -184,8 +204,11 @@ static void shell_walk_k(const orc_geom* g, orc_ws* w, int j, int h, int m, int 
     double u = -hz + k * g->dz - zc; /* slab plane offset */
     if (fabs(u) < ell) tb[n++] = atan2(sqrt((ell - u) * (ell + u)), u);
   }
-  for (int l = 0; l <= g->n_ell; ++l) {
-    double rb = g->ell_lo + l * dl; /* radius-bin edge */
+  const int nr = g->rho_linear ? g->n_ell + 2 : g->n_ell + 1;
+  for (int i = 0; i < nr; ++i) {
+    double rb; /* radius-bin edge, or lo / node / hi */
+    if (!g->rho_linear) rb = g->ell_lo + i * dl;
+    else rb = i == 0 ? g->ell_lo : (i == nr - 1 ? g->ell_hi : ell_centre(g, i - 1));
     if (rb > 0.0 && rb < ell) {
       double a = atan2(rb, sqrt((ell - rb) * (ell + rb)));
       tb[n++] = a;
@@ -193,22 +216,83 @@ static void shell_walk_k(const orc_geom* g, orc_ws* w, int j, int h, int m, int 
     }
   }
   qsort(tb, n, sizeof(double), cmp_double);
-  w->cl = -1;
+  return n;
+}
+
+/* Weights of the t-segment [t0, t1] of the semicircle of radius ell on the
+ * intermediate's radius pieces: up to two (radius index, weight) pairs.
+ * Returns how many (0 when the segment lies outside [lo, hi]). */
+static int segment_weights(const orc_geom* g, double ell, double t0, double t1, int* idx,
+                           double* wt) {
+  const double dl = dell(g);
+  const double tm = 0.5 * (t0 + t1), rho = ell * sin(tm);
+  const double L = ell * (t1 - t0); /* arc length in the (z, rho) plane */
+  if (!g->rho_linear) {
+    int l = (int)floor((rho - g->ell_lo) / dl);
+    if (l < 0 || l >= g->n_ell) return 0;
+    idx[0] = l;
+    wt[0] = L;
+    return 1;
+  }
+  if (rho <= g->ell_lo || rho >= g->ell_hi) return 0;
+  const double u = (rho - ell_centre(g, 0)) / dl;
+  if (u < 0.0 || g->n_ell == 1) { /* below the first node: constant */
+    idx[0] = 0;
+    wt[0] = L;
+    return 1;
+  }
+  if (u >= g->n_ell - 1) { /* above the last node: constant */
+    idx[0] = g->n_ell - 1;
+    wt[0] = L;
+    return 1;
+  }
+  int l = (int)floor(u);
+  if (l > g->n_ell - 2) l = g->n_ell - 2;
+  /* int rho ds = ell^2 (cos t0 - cos t1), written without cancellation */
+  const double M = 2.0 * ell * ell * sin(tm) * sin(0.5 * (t1 - t0));
+  idx[0] = l;
+  wt[0] = (ell_centre(g, l + 1) * L - M) / dl;
+  idx[1] = l + 1;
+  wt[1] = (M - ell_centre(g, l) * L) / dl;
+  return 2;
+}
+
+/* In-plane circle of sensor (sx, sy) at the centre radius of bin l, from the
+ * two-slot cache (slot `avoid` is kept for the other radius of a segment). */
+static int cached_circle(const orc_geom* g, orc_ws* w, double sx, double sy, int l, int avoid) {
+  for (int c = 0; c < 2; ++c)
+    if (w->cl[c] == l) return c;
+  int c = avoid == 0 ? 1 : 0;
+  w->cn[c] = circle_walk(g, sx, sy, ell_centre(g, l), w->ab, w->cpix[c], w->clen[c]);
+  w->cl[c] = l;
+  return c;
+}
+
+static void shell_walk_k(const orc_geom* g, orc_ws* w, int j, int h, int m, int k_lo, int k_hi,
+                         emit_fn emit, void* ctx) {
+  const double hz = half_z(g);
+  const double ell = ell_centre(g, m), zc = ring_z(g, h);
+  const double sx = sensor_x(g, j), sy = sensor_y(g, j);
+  double* tb = w->tb;
+  const int n = shell_breaks(g, ell, zc, tb);
+  w->cl[0] = w->cl[1] = -1;
   for (int s = 0; s + 1 < n; ++s) {
     double t0 = tb[s], t1 = tb[s + 1];
     if (!(t1 > t0)) continue;
     double tm = 0.5 * (t0 + t1);
-    double z = zc + ell * cos(tm), rho = ell * sin(tm);
+    double z = zc + ell * cos(tm);
     int k = (int)floor((z + hz) / g->dz);
-    int l = (int)floor((rho - g->ell_lo) / dl);
-    if (k < k_lo || k >= k_hi || l < 0 || l >= g->n_ell) continue;
-    double wt = ell * (t1 - t0); /* arc length in the (z, rho) plane */
-    if (l != w->cl) {            /* in-plane circle for bin l, radius rho_l */
-      w->cn = circle_walk(g, sx, sy, ell_centre(g, l), w->ab, w->cpix, w->clen);
-      w->cl = l;
+    if (k < k_lo || k >= k_hi) continue;
+    int idx[2];
+    double wt[2];
+    const int nw = segment_weights(g, ell, t0, t1, idx, wt);
+    int used = -1;
+    for (int i = 0; i < nw; ++i) {
+      const int c = cached_circle(g, w, sx, sy, idx[i], used);
+      used = c;
+      for (int q = 0; q < w->cn[c]; ++q)
+        emit(ctx, (long)w->cpix[c][q] * g->mz + k, wt[i] * w->clen[c][q]);
     }
-    for (int q = 0; q < w->cn; ++q)
-      emit(ctx, (long)w->cpix[q] * g->mz + k, wt * w->clen[q]);
   }
 }
 
@@ -435,42 +519,31 @@ int orc_circle_arcs(const orc_geom* g, int j, int l, int32_t* pix, double* len, 
  * (slab k, radius bin l) cell, one entry per t-segment, cell = l*mz + k.  */
 int orc_semicircle_arcs(const orc_geom* g, int h, int m, int32_t* cell, double* len, int cap) {
   if (check_geom(g)) return -1;
-  const double hz = half_z(g), dl = dell(g);
+  const double hz = half_z(g);
   const double ell = ell_centre(g, m), zc = ring_z(g, h);
-  int nt = 2 * (g->mz + 1) + 2 * (g->n_ell + 1) + 4;
+  int nt = 2 * (g->mz + 1) + 2 * (g->n_ell + 2) + 4;
   double* tb = (double*)malloc(sizeof(double) * nt);
   if (!tb) return -2;
-  int n = 0;
-  tb[n++] = 0.0;
-  tb[n++] = ORC_PI;
-  for (int k = 0; k <= g->mz; ++k) {
-    double u = -hz + k * g->dz - zc;
-    if (fabs(u) < ell) tb[n++] = atan2(sqrt((ell - u) * (ell + u)), u);
-  }
-  for (int l = 0; l <= g->n_ell; ++l) {
-    double rb = g->ell_lo + l * dl;
-    if (rb > 0.0 && rb < ell) {
-      double a = atan2(rb, sqrt((ell - rb) * (ell + rb)));
-      tb[n++] = a;
-      tb[n++] = ORC_PI - a;
-    }
-  }
-  qsort(tb, n, sizeof(double), cmp_double);
+  const int n = shell_breaks(g, ell, zc, tb);
   int out = 0;
   for (int s = 0; s + 1 < n; ++s) {
     double t0 = tb[s], t1 = tb[s + 1];
     if (!(t1 > t0)) continue;
     double tm = 0.5 * (t0 + t1);
     int k = (int)floor((zc + ell * cos(tm) + hz) / g->dz);
-    int l = (int)floor((ell * sin(tm) - g->ell_lo) / dl);
-    if (k < 0 || k >= g->mz || l < 0 || l >= g->n_ell) continue;
-    if (out >= cap) {
-      free(tb);
-      return -3;
+    if (k < 0 || k >= g->mz) continue;
+    int idx[2];
+    double wt[2];
+    const int nw = segment_weights(g, ell, t0, t1, idx, wt);
+    for (int i = 0; i < nw; ++i) {
+      if (out >= cap) {
+        free(tb);
+        return -3;
+      }
+      cell[out] = idx[i] * g->mz + k;
+      len[out] = wt[i];
+      ++out;
     }
-    cell[out] = l * g->mz + k;
-    len[out] = ell * (t1 - t0);
-    ++out;
   }
   free(tb);
   return out;
@@ -479,8 +552,18 @@ int orc_semicircle_arcs(const orc_geom* g, int h, int m, int32_t* cell, double* 
 /* --------------------------------------------- per-voxel weight path
  * Arc length of the circle (cx, cy, r) inside the box [x0,x1] x [y0,y1]:
  * breakpoints where the circle meets the four box lines, midpoint test.    */
+static double arc_in_box_m(double cx, double cy, double r, double x0, double x1, double y0,
+                           double y1, double* moment);
+
 static double arc_in_box(double cx, double cy, double r, double x0, double x1, double y0,
                          double y1) {
+  return arc_in_box_m(cx, cy, r, x0, x1, y0, y1, NULL);
+}
+
+/* The same, and *moment = int y ds over those arcs (y = cy + r sin a, so
+ * int y ds = r cy (a1 - a0) + r^2 (cos a0 - cos a1) per arc). */
+static double arc_in_box_m(double cx, double cy, double r, double x0, double x1, double y0,
+                           double y1, double* moment) {
   double ab[8];
   int n = 0;
   double xs[2] = {x0, x1}, ys[2] = {y0, y1};
@@ -499,7 +582,7 @@ static double arc_in_box(double cx, double cy, double r, double x0, double x1, d
     }
   }
   qsort(ab, n, sizeof(double), cmp_double);
-  double acc = 0.0;
+  double acc = 0.0, mom = 0.0;
   int nseg = n > 0 ? n : 1;
   for (int s = 0; s < nseg; ++s) {
     double a0, a1;
@@ -513,8 +596,12 @@ static double arc_in_box(double cx, double cy, double r, double x0, double x1, d
     if (!(a1 > a0)) continue;
     double am = 0.5 * (a0 + a1);
     double x = cx + r * cos(am), y = cy + r * sin(am);
-    if (x > x0 && x < x1 && y > y0 && y < y1) acc += r * (a1 - a0);
+    if (x > x0 && x < x1 && y > y0 && y < y1) {
+      acc += r * (a1 - a0);
+      mom += r * cy * (a1 - a0) + 2.0 * r * r * sin(am) * sin(0.5 * (a1 - a0));
+    }
   }
+  if (moment) *moment = mom;
   return acc;
 }
 
@@ -522,9 +609,39 @@ double orc_arc_in_box(double cx, double cy, double r, double x0, double x1, doub
   return arc_in_box(cx, cy, r, x0, x1, y0, y1);
 }
 
+/* Weight of the intermediate's value at (slab k, radius l) in the (z, rho)
+ * semicircle (centre (zc, 0), radius ell): piecewise constant, the arc in the
+ * cell [z0, z0 + dz] x [bin l]; piecewise linear, the hat of node rho_l
+ * integrated along the arc in the slab (pieces [rho_{l-1}, rho_l] and
+ * [rho_l, rho_{l+1}], constant pieces [lo, rho_0] and [rho_{n-1}, hi]). */
+static double semicircle_weight(const orc_geom* g, double zc, double ell, double z0, int l) {
+  const double dl = dell(g);
+  if (!g->rho_linear) {
+    double rb0 = g->ell_lo + l * dl;
+    return arc_in_box(zc, 0.0, ell, z0, z0 + g->dz, rb0, rb0 + dl);
+  }
+  const double rl = ell_centre(g, l);
+  double acc = 0.0, L, M;
+  if (l == 0) {
+    acc += arc_in_box(zc, 0.0, ell, z0, z0 + g->dz, g->ell_lo, rl);
+  } else {
+    const double ra = ell_centre(g, l - 1);
+    L = arc_in_box_m(zc, 0.0, ell, z0, z0 + g->dz, ra, rl, &M);
+    acc += (M - ra * L) / dl;
+  }
+  if (l == g->n_ell - 1) {
+    acc += arc_in_box(zc, 0.0, ell, z0, z0 + g->dz, rl, g->ell_hi);
+  } else {
+    const double rb = ell_centre(g, l + 1);
+    L = arc_in_box_m(zc, 0.0, ell, z0, z0 + g->dz, rl, rb, &M);
+    acc += (rb * L - M) / dl;
+  }
+  return acc;
+}
+
 /* Weight of voxel (ix, iy, k) in shell (j, h, m):
- *   sum over radius bins l of  [arc of the (z,rho) semicircle in cell (k,l)]
- *                            x [arc of the in-plane circle rho_l in pixel].  */
+ *   sum over radius indices l of [weight of (k, l) in the (z,rho) semicircle]
+ *                              x [arc of the in-plane circle rho_l in pixel]. */
 static double point_weight(const orc_geom* g, int j, int h, int m, int ix, int iy, int k) {
   const double hx = half_x(g), hz = half_z(g), dl = dell(g);
   const double sx = sensor_x(g, j), sy = sensor_y(g, j);
@@ -546,9 +663,7 @@ static double point_weight(const orc_geom* g, int j, int h, int m, int ix, int i
     double rho = ell_centre(g, l);
     double a1 = arc_in_box(sx, sy, rho, px0, px0 + g->dxy, py0, py0 + g->dxy);
     if (a1 == 0.0) continue;
-    double rb0 = g->ell_lo + l * dl;
-    double a2 = arc_in_box(zc, 0.0, ell, z0, z0 + g->dz, rb0, rb0 + dl);
-    acc += a1 * a2;
+    acc += a1 * semicircle_weight(g, zc, ell, z0, l);
   }
   return acc;
 }

@@ -51,6 +51,55 @@ def arc_circle_rect(cx, cy, r, x0, x1, y0, y1) -> float:
     return r * t
 
 
+def _ov_iv(*iv):
+    lo = max(a for a, _ in iv)
+    hi = min(b for _, b in iv)
+    return (lo, hi) if hi > lo else None
+
+
+def moment_circle_rect(cx, cy, r, x0, x1, y0, y1) -> float:
+    """int y ds over the part of the circle (cx, cy, r) inside [x0, x1] x
+    [y0, y1]: on each quarter interval [t0, t1] of t (x = cx + r cos t,
+    y = cy + r sin t), r cy (t1 - t0) + r^2 (cos t0 - cos t1)."""
+    a1, a0 = _acos_r(x1 - cx, r), _acos_r(x0 - cx, r)
+    s0, s1 = _asin_r(y0 - cy, r), _asin_r(y1 - cy, r)
+    ivs = [_ov_iv((0.0, 0.5 * PI), (a1, a0), (s0, s1)),
+           _ov_iv((0.5 * PI, PI), (a1, a0), (PI - s1, PI - s0)),
+           _ov_iv((-PI, -0.5 * PI), (-a0, -a1), (-PI - s1, -PI - s0)),
+           _ov_iv((-0.5 * PI, 0.0), (-a0, -a1), (s0, s1))]
+    m = 0.0
+    for iv in ivs:
+        if iv is not None:
+            t0, t1 = iv
+            m += r * cy * (t1 - t0) + r * r * (math.cos(t0) - math.cos(t1))
+    return m
+
+
+def hat_weight_semicircle(zh, ell, z0, z1, nodes, lo, hi, l) -> float:
+    """The hat of radius node l (piecewise-linear interpolation between the
+    nodes, constant below the first and above the last, zero outside
+    [lo, hi]) integrated along the (z, rho) semicircle of ring zh and radius
+    ell inside the slab [z0, z1]."""
+    n, dl = len(nodes), nodes[1] - nodes[0] if len(nodes) > 1 else hi - lo
+    rl = nodes[l]
+    acc = 0.0
+    if l == 0:
+        acc += arc_circle_rect(zh, 0.0, ell, z0, z1, lo, rl)
+    else:
+        ra = nodes[l - 1]
+        L = arc_circle_rect(zh, 0.0, ell, z0, z1, ra, rl)
+        M = moment_circle_rect(zh, 0.0, ell, z0, z1, ra, rl)
+        acc += (M - ra * L) / dl
+    if l == n - 1:
+        acc += arc_circle_rect(zh, 0.0, ell, z0, z1, rl, hi)
+    else:
+        rb = nodes[l + 1]
+        L = arc_circle_rect(zh, 0.0, ell, z0, z1, rl, rb)
+        M = moment_circle_rect(zh, 0.0, ell, z0, z1, rl, rb)
+        acc += (rb * L - M) / dl
+    return acc
+
+
 def ball_srt(sensor, centre, a, amp, ell) -> np.ndarray:
     """Closed-form SRT of a uniform ball: area of the spherical cap of the shell
     |x - sensor| = ell inside the ball, times amp.  Cap area 2*pi*ell*h with
