@@ -225,8 +225,15 @@ static int shell_breaks(const orc_geom* g, double ell, double zc, double* tb) {
 static int segment_weights(const orc_geom* g, double ell, double t0, double t1, int* idx,
                            double* wt) {
   const double dl = dell(g);
-  const double tm = 0.5 * (t0 + t1), rho = ell * sin(tm);
+  const double tm = 0.5 * (t0 + t1);
   const double L = ell * (t1 - t0); /* arc length in the (z, rho) plane */
+  /* The piece is chosen by the middle of the segment's rho range, not by rho
+   * at its middle t: the radius grid meets the semicircle at its top (where
+   * ell is itself a node, rho = ell only at t = pi/2), and a segment ending
+   * or centred there has rho(tm) = ell, on the node, although it lies below. */
+  const double s0 = sin(t0), s1 = sin(t1);
+  const double smax = (t0 < 0.5 * ORC_PI && t1 > 0.5 * ORC_PI) ? 1.0 : fmax(s0, s1);
+  const double rho = 0.5 * ell * (fmin(s0, s1) + smax);
   if (!g->rho_linear) {
     int l = (int)floor((rho - g->ell_lo) / dl);
     if (l < 0 || l >= g->n_ell) return 0;
@@ -567,15 +574,18 @@ static double arc_in_box_m(double cx, double cy, double r, double x0, double x1,
   double ab[8];
   int n = 0;
   double xs[2] = {x0, x1}, ys[2] = {y0, y1};
+  /* A line the circle touches (|u| = r) also gives a breakpoint, at the
+   * point of contact: otherwise the midpoint of the arc around that point
+   * would lie on the line and fail the open-box test below. */
   for (int i = 0; i < 2; ++i) {
     double u = xs[i] - cx;
-    if (fabs(u) < r) {
+    if (fabs(u) <= r) {
       double v = sqrt((r - u) * (r + u));
       ab[n++] = wrap_2pi(atan2(v, u));
       ab[n++] = wrap_2pi(atan2(-v, u));
     }
     u = ys[i] - cy;
-    if (fabs(u) < r) {
+    if (fabs(u) <= r) {
       double v = sqrt((r - u) * (r + u));
       ab[n++] = wrap_2pi(atan2(u, v));
       ab[n++] = wrap_2pi(atan2(u, -v));

@@ -48,7 +48,12 @@ def _grid(g):
 
 
 def test_semicircle_hat_weights_closed_form(orc):
-    for g in (_tiny(orc), _tiny(orc, n_ell=1), _tiny(orc, n_ell=2, zs_lo=-0.9, zs_hi=0.9)):
+    """Includes rings at the slab centres (n_zs = mz over the volume height):
+    there every semicircle's slab breaks are symmetric about its top, where it
+    touches its own radius node, the case a t-midpoint test misplaces."""
+    for g in (_tiny(orc), _tiny(orc, n_ell=1), _tiny(orc, n_ell=2, zs_lo=-0.9, zs_hi=0.9),
+              _tiny(orc, n_zs=4, zs_lo=-0.9, zs_hi=0.9),
+              _tiny(orc, mz=5, n_zs=5, zs_lo=-1.125, zs_hi=1.125, n_ell=7)):
         G = _grid(g)
         checked = 0
         for h in range(g.n_zs):
@@ -113,8 +118,10 @@ def test_separable_volume_closed_form(orc):
     assert np.count_nonzero(want) > 0.3 * want.size
 
 
-def test_point_weights_adjoint_identity(orc):
-    g = _tiny(orc, ms=6, mz=5, n_ell=14)
+@pytest.mark.parametrize("centred", [False, True])
+def test_point_weights_adjoint_identity(orc, centred):
+    g = _tiny(orc, ms=6, mz=5, n_ell=14, **(dict(n_zs=5, zs_lo=-1.125, zs_hi=1.125)
+                                           if centred else {}))
     rng = np.random.default_rng(3)
     checked = 0
     for _ in range(8):
