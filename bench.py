@@ -46,6 +46,8 @@ def parse():
                    help="store A2, A2^T as CSR instead of applying them from the Toeplitz taps")
     p.add_argument("--a1-rotation", action="store_true",
                    help="store A1 for a quarter of the sensor columns (4x smaller, slower)")
+    p.add_argument("--rho-linear", action="store_true",
+                   help="piecewise-linear intermediate in rho (else constant on the radius bins)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=10)
     return p.parse_args()
@@ -225,14 +227,14 @@ def workload_config(name, geom, batch, weights, extra=None):
     return cfg
 
 
-def cpu_oracle_rate(name, budget_s, seed=5):
+def cpu_oracle_rate(name, budget_s, seed=5, rho_linear=False):
     """Oracle forward + adjoint on a seeded shell sample sized to budget_s;
     returns (pairs/s extrapolated to the full workload, threads, sample text)."""
     import numpy as np
     from oracle import oracle as O
     from paper_2402_15641_gb300 import inputs as I
     sz = I.sizes(name)
-    g = O.OracleGeometry.default(**sz)
+    g = O.OracleGeometry.default(**sz, rho_linear=rho_linear)
     f = I.phantom(name)
     y = I.probe(name)
     total = g.n_phi * g.n_zs * g.n_ell
@@ -264,7 +266,7 @@ def run_reference(args):
     from paper_2402_15641_gb300 import inputs as I
     import numpy as np
     sz = I.sizes(args.workload)
-    g = O.OracleGeometry.default(**sz)
+    g = O.OracleGeometry.default(**sz, rho_linear=args.rho_linear)
     f = I.phantom(args.workload)
     y = I.probe(args.workload)
     total = g.n_phi * g.n_zs * g.n_ell
@@ -322,7 +324,7 @@ def run_ours(args):
     pk = peaks()
     sz = I.sizes(args.workload)
     geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only,
-                               a1_rotation=args.a1_rotation)
+                               a1_rotation=args.a1_rotation, rho_linear=args.rho_linear)
     B = args.batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -442,11 +444,13 @@ def run_ours(args):
                                                   if plan.info["a2_taps"] else "CSR"),
                                       "a1_form": ("CSR of the first n_phi/4 columns, the rest "
                                                   "by rotation" if plan.info["a1_rot"] else "CSR"),
-                                      "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3)}),
+                                      "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3),
+                                      "intermediate": ("piecewise linear in rho" if args.rho_linear
+                                                       else "piecewise constant on radius bins")}),
            "roofline": roof, "hbm": hbm, "stages": stages, "clocks": clk, "e2e": e2e,
            "gpu_launches": launches}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, n, t = cpu_oracle_rate(args.workload, 15.0)
+        rate, cores, n, t = cpu_oracle_rate(args.workload, 15.0, rho_linear=args.rho_linear)
         out["cpu_baseline"] = {
             "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle forward + adjoint over {n} seeded shells of "

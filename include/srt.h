@@ -54,6 +54,14 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  * with rot(ix, iy) = (ms-1-iy, ix).  A1's memory drops 4x; the A1 product is
  * ~3% and the A1^T product ~11% slower at 256^3 (srt_plan_info_t.a1_rot). */
 #define SRT_A1_ROTATION 0x8
+/* SRT_RHO_LINEAR: the intermediate f^{1,2} is piecewise linear in rho instead
+ * of constant on the radius bins (Sec. 3.1 notes the method carries over to
+ * other bases): linear between the nodes rho_i = ell_lo + (i + 1/2) d,
+ * constant from ell_lo to rho_0 and from rho_{n_ell-1} to ell_hi, zero
+ * outside [ell_lo, ell_hi].  A1 is unchanged (it samples f^{1,2} at the
+ * nodes); A2's entry (l, k) becomes node l's hat integrated along the
+ * semicircle inside slab k, so A2 holds about twice the entries. */
+#define SRT_RHO_LINEAR 0x10
 /* When the rings sit at the slab centres (n_zs = mz over the volume height),
  * A2[(h,m),(l,k)] = T[m, k-h, l] for a master tensor T, and the plan applies A2
  * and A2^T from T's taps without storing them (srt_plan_info_t.a2_taps = 1),

@@ -17,6 +17,7 @@ SRT_FP32, SRT_BF16 = 0, 1
 SRT_KEEP_F64 = 1
 SRT_CSR_ONLY = 2
 SRT_A1_ROTATION = 8
+SRT_RHO_LINEAR = 16
 SRT_NOALLOC_WORKSPACE_BYTES = 32 << 20
 
 

@@ -11,6 +11,10 @@
 //   the semicircle inside the cell (vertical CRT, measure l dt, Sec. 2).
 //   Every cell has rho >= ell_lo > 0, so the full circle's lower half never
 //   meets a cell and the full-circle arc length equals the semicircle's.
+//   With SRT_RHO_LINEAR the intermediate is piecewise linear in rho (the basis
+//   remark of Sec. 3.1): column c = l*mz + k is node l's hat on slab k and the
+//   entry is the hat integrated along the semicircle there (hat_weight); A1 is
+//   unchanged (its circles sit at the nodes).
 //
 // Lengths are computed in FP64 (srt_arc_in_rect), rounded once to the stored
 // type.  Rows are enumerated strip by strip (pixel columns for A1, radius bins
@@ -29,7 +33,8 @@ constexpr unsigned FULL = 0xffffffffu;
 
 struct GeomDev {
   int ms, mz, n_phi, n_zs, n_ell;
-  int nj;  // sensor columns whose A1 rows are assembled (the first nj of n_phi)
+  int nj;       // sensor columns whose A1 rows are assembled (the first nj of n_phi)
+  int rho_lin;  // A2 columns are hats of the radius nodes (else bins)
   double dxy, dz, radius, phi0, zs_lo, zs_hi, ell_lo, ell_hi;
   double hx, hz, dl, thr1, thr2;
 };
@@ -40,6 +45,7 @@ GeomDev make_geom(const srt_geometry& g) {
   G.mz = g.mz;
   G.n_phi = g.n_phi;
   G.nj = g.n_phi;
+  G.rho_lin = (g.flags & SRT_RHO_LINEAR) ? 1 : 0;
   G.n_zs = g.n_zs;
   G.n_ell = g.n_ell;
   G.dxy = g.dxy;
@@ -68,6 +74,32 @@ __device__ __forceinline__ void cover(double a, double b, double half, double d,
   hi = clampi((int)floor((b + half) / d) + 1, 0, n - 1);
 }
 
+// Piecewise-linear intermediate: the hat of radius node l (linear between
+// the nodes rho_i = ell_lo + (i + 1/2) dl, constant from ell_lo to rho_0 and
+// from rho_{n-1} to ell_hi) integrated along the (z, rho) semicircle of centre
+// (zc, 0) and radius r inside the slab [c0, c1].  On [rho_a, rho_b] = [rho_{l-1},
+// rho_l] the hat is (rho - rho_a)/dl, so its integral is (M - rho_a L)/dl with L
+// the arc length and M = int rho ds there; likewise (rho_b L - M)/dl above.
+__device__ double hat_weight(const GeomDev& G, double zc, double r, int l, double c0, double c1) {
+  const double rl = G.ell_lo + (l + 0.5) * G.dl;
+  double w = 0.0, m = 0.0;
+  if (l == 0) {
+    w += srt_arc_in_rect(zc, 0.0, r, c0, c1, G.ell_lo, rl);
+  } else {
+    const double ra = G.ell_lo + (l - 0.5) * G.dl;
+    const double len = srt_arc_in_rect_m(zc, 0.0, r, c0, c1, ra, rl, &m);
+    w += (m - ra * len) / G.dl;
+  }
+  if (l == G.n_ell - 1) {
+    w += srt_arc_in_rect(zc, 0.0, r, c0, c1, rl, G.ell_hi);
+  } else {
+    const double rb = G.ell_lo + (l + 1.5) * G.dl;
+    const double len = srt_arc_in_rect_m(zc, 0.0, r, c0, c1, rl, rb, &m);
+    w += (rb * len - m) / G.dl;
+  }
+  return w;
+}
+
 // Enumerate one strip.  The strip spans [s0, s1] along the strip axis; the
 // circle (centre (cu, cv) in (strip axis, cross axis), radius r) has two
 // branches over it.  For every candidate cross index q (ascending) the exact
@@ -83,9 +115,15 @@ __device__ int strip_enum(const GeomDev& G, double cu, double cv, double r, int 
     half = G.hx;
     d = G.dxy;
     n = G.ms;
-  } else {  // strip = radius bin l, cross axis = z
+  } else if (!G.rho_lin) {  // strip = radius bin l, cross axis = z
     s0 = G.ell_lo + s * G.dl;
     s1 = G.ell_lo + (s + 1) * G.dl;
+    half = G.hz;
+    d = G.dz;
+    n = G.mz;
+  } else {  // strip = support of node l's hat
+    s0 = s == 0 ? G.ell_lo : G.ell_lo + (s - 0.5) * G.dl;
+    s1 = s == G.n_ell - 1 ? G.ell_hi : G.ell_lo + (s + 1.5) * G.dl;
     half = G.hz;
     d = G.dz;
     n = G.mz;
@@ -109,8 +147,10 @@ __device__ int strip_enum(const GeomDev& G, double cu, double cv, double r, int 
       double w;
       if (A1)
         w = srt_arc_in_rect(cu, cv, r, s0, s1, c0, c1);
-      else  // (z, rho) plane: x = z, y = rho
+      else if (!G.rho_lin)  // (z, rho) plane: x = z, y = rho
         w = srt_arc_in_rect(cv, cu, r, c0, c1, s0, s1);
+      else
+        w = hat_weight(G, cv, r, s, c0, c1);
       if (w > thr) {
         f(q, w, kept);
         ++kept;

@@ -150,6 +150,31 @@ __host__ __device__ inline double srt_arc_in_rect(double cx, double cy, double r
   return r * t;
 }
 
+// Length of the circle (cx, cy, r) inside the box (the return value) and its
+// first moment int y ds there (*my), from the same quarter intervals: on an
+// interval [t0, t1] of y = cy + r sin t, the moment is r cy (t1 - t0) +
+// r^2 (cos t0 - cos t1), the last factor taken as 2 sin(tm) sin(dt/2).
+__host__ __device__ inline double srt_arc_in_rect_m(double cx, double cy, double r, double x0,
+                                                    double x1, double y0, double y1, double* my) {
+  const double hp = 0.5 * SRT_PI;
+  const double a1 = srt_acos_r(x1 - cx, r), a0 = srt_acos_r(x0 - cx, r);
+  const double s0 = srt_asin_r(y0 - cy, r), s1 = srt_asin_r(y1 - cy, r);
+  const double lo[4] = {fmax(0.0, fmax(a1, s0)), fmax(hp, fmax(a1, SRT_PI - s1)),
+                        fmax(-SRT_PI, fmax(-a0, -SRT_PI - s1)), fmax(-hp, fmax(-a0, s0))};
+  const double hi[4] = {fmin(hp, fmin(a0, s1)), fmin(SRT_PI, fmin(a0, SRT_PI - s0)),
+                        fmin(-hp, fmin(-a1, -SRT_PI - s0)), fmin(0.0, fmin(-a1, s1))};
+  double t = 0.0, m = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    if (hi[i] > lo[i]) {
+      const double dt = hi[i] - lo[i];
+      t += dt;
+      m += r * cy * dt + 2.0 * r * r * sin(0.5 * (lo[i] + hi[i])) * sin(0.5 * dt);
+    }
+  }
+  *my = m;
+  return r * t;
+}
+
 // Round an FP64 value to BF16 (round to nearest, ties to even) in one step,
 // from the FP64 bit pattern: keep 7 fraction bits, round on the other 45.
 // Values below the BF16 normal range flush to signed zero (entries here are

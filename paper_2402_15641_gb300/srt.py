@@ -41,11 +41,12 @@ class Geometry:
     keep_f64: bool = False
     csr_only: bool = False
     a1_rotation: bool = False
+    rho_linear: bool = False  # intermediate piecewise linear in rho (else constant on bins)
 
     @staticmethod
     def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, **options) -> "Geometry":
         """Default readings, computed by the library (srt_geometry_default);
-        options set weight_dtype / keep_f64 / csr_only / a1_rotation."""
+        options set weight_dtype / keep_f64 / csr_only / a1_rotation / rho_linear."""
         g = L.SrtGeometry()
         check(L.lib().srt_geometry_default(ctypes.byref(g), ms, mz, dxy, dz, radius, n_phi, n_zs,
                                            n_ell), "srt_geometry_default")
@@ -67,7 +68,8 @@ class Geometry:
                              self.ell_lo, self.ell_hi, wd,
                              (L.SRT_KEEP_F64 if self.keep_f64 else 0)
                              | (L.SRT_CSR_ONLY if self.csr_only else 0)
-                             | (L.SRT_A1_ROTATION if self.a1_rotation else 0))
+                             | (L.SRT_A1_ROTATION if self.a1_rotation else 0)
+                             | (L.SRT_RHO_LINEAR if self.rho_linear else 0))
 
     @property
     def f_shape(self):

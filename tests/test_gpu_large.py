@@ -74,19 +74,23 @@ def srt256_inputs():
     return I.crop_phantom("srt256", 64), I.probe("srt256")
 
 
-@pytest.mark.parametrize("wdt,tol,csr", [("fp32", 1e-5, False), ("bf16", 5e-3, False),
-                                         ("fp32", 1e-5, True)])
-def test_srt256_crop_sampled(srt, orc, srt256_inputs, wdt, tol, csr):
-    """The benchmark's configuration (A2 from the Toeplitz taps) and the CSR
-    form of A2, against the oracle on samples of the 64^3-crop workload."""
+@pytest.mark.parametrize("wdt,tol,csr,lin", [("fp32", 1e-5, False, False),
+                                             ("bf16", 5e-3, False, False),
+                                             ("fp32", 1e-5, True, False),
+                                             ("fp32", 1e-5, False, True)])
+def test_srt256_crop_sampled(srt, orc, srt256_inputs, wdt, tol, csr, lin):
+    """The benchmark's configuration (A2 from the Toeplitz taps), the CSR
+    form of A2 and the piecewise-linear intermediate, against the oracle on
+    samples of the 64^3-crop workload."""
     sz = dict(I.sizes("srt256"))
-    g, o = geom_pair(orc, weight_dtype=wdt, csr_only=csr, **sz)
+    g, o = geom_pair(orc, weight_dtype=wdt, csr_only=csr, rho_linear=lin, **sz)
     plan = srt.Plan(g)
     f, y = srt256_inputs
     sh, vx = _samples(g, 4096, 96, 41, crop=64)
     e_p, e_a = _check(srt, orc, plan, o, f, y, sh, vx, tol)
-    print(f"PARITY srt256 {wdt}{' csr' if csr else ''} (64^3 crop, 4096 shells, 96 voxels):"
-          f" forward rel-L2 {e_p:.3e}, adjoint rel-L2 {e_a:.3e}")
+    print(f"PARITY srt256 {wdt}{' csr' if csr else ''}{' rho-linear' if lin else ''}"
+          f" (64^3 crop, 4096 shells, 96 voxels): forward rel-L2 {e_p:.3e},"
+          f" adjoint rel-L2 {e_a:.3e}")
     fd, yd = to_dev(f), to_dev(y)
     af, aty = plan.forward(fd), plan.adjoint(yd)
     lhs, rhs = srt.dot_f64(af, yd), srt.dot_f64(fd, aty)
