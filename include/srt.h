@@ -180,6 +180,48 @@ int srt_adjoint_host(srt_plan_t plan, const float* p_host, float* f_host, int32_
                      void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Pipelined host-buffer calls: a sequence of forward and adjoint calls on
+ * HOST buffers with up to two in flight, so that one call's input copy
+ * overlaps the previous call's computation and its result copy (one copy,
+ * after the transform) overlaps the next call's.  Results are bitwise those of srt_forward_host /
+ * srt_adjoint_host.  (The paper has no counterpart; this is the serving-side
+ * form of the host-buffer calls.)
+ *   srt_pipe_create: device buffers for two calls of `batch` volumes (two
+ *     input and two output slots of the larger of f and p, plus one
+ *     transform workspace) and three streams of its own (input copies,
+ *     computation, result copies).  Errors: SRT_ERR_ARG, SRT_ERR_OOM,
+ *     SRT_ERR_CUDA; on error *pipe is set to NULL.
+ *   srt_pipe_submit: enqueue one call (direction 0 = forward, f_host ->
+ *     p_host; 1 = adjoint, p_host -> f_host) and return without waiting;
+ *     *ticket (may be NULL) numbers the calls 0, 1, 2, ...  Call i uses slot
+ *     i % 2 and starts its input copy once call i - 2 has consumed that
+ *     slot's input.  in_host and out_host must stay allocated and unchanged
+ *     (out_host unread) until srt_pipe_wait(ticket) has returned SRT_OK;
+ *     pinned memory gives full copy speed.  The calls run in submission
+ *     order.  Errors: SRT_ERR_ARG (null pipe or buffer, bad direction),
+ *     SRT_ERR_CUDA.
+ *   srt_pipe_wait: block until call `ticket`'s result is in its host buffer
+ *     (polling, at most timeout_s seconds; a negative timeout waits without
+ *     limit).  Errors: SRT_ERR_ARG (unknown ticket), SRT_ERR_TIMEOUT,
+ *     SRT_ERR_CUDA (a failure in this or an earlier call of the pipe).
+ *   srt_pipe_stage_times: for a finished call among the last 8 submitted,
+ *     ms[0..3] = input copy,
+ *     transform and result copy durations, and the idle time of the compute
+ *     stream between the previous call's transform and this one's (0 for
+ *     the first call), in milliseconds from CUDA events.  Errors:
+ *     SRT_ERR_ARG, SRT_ERR_NOT_READY (not finished, or older than the last 8).
+ *   srt_pipe_destroy: wait for every call, then free the pipe (NULL is a
+ *     no-op).  Not thread safe: one host thread drives a pipe.
+ */
+typedef struct srt_pipe_s* srt_pipe_t;
+int srt_pipe_create(srt_plan_t plan, int32_t batch, srt_pipe_t* pipe);
+int srt_pipe_submit(srt_pipe_t pipe, int32_t direction, const float* in_host, float* out_host,
+                    int64_t* ticket);
+int srt_pipe_wait(srt_pipe_t pipe, int64_t ticket, double timeout_s);
+int srt_pipe_stage_times(srt_pipe_t pipe, int64_t ticket, float* ms);
+int srt_pipe_destroy(srt_pipe_t pipe);
+
+/*
  * Forward transform that allocates nothing, for callers that cannot hand the
  * library a device workspace: programs whose device memory is owned by another
  * allocator that forbids direct cudaMalloc/cudaFree, code running in callbacks

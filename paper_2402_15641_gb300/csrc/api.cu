@@ -11,7 +11,9 @@
 // Adjoint (Alg. 2): P2^-1, A2^T, P1^-1, A1^T with the transposed matrices.
 #include <math.h>
 #include <algorithm>
+#include <chrono>
 #include <new>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -78,7 +80,9 @@ constexpr int kHostChunks = 4;
 struct HostSink {
   float* host = nullptr;
   cudaStream_t cs = nullptr;
+  int chunks = kHostChunks;  // 1: the whole result in one copy after the transform
   cudaEvent_t ev[kHostChunks] = {};
+  cudaEvent_t t0 = nullptr;  // when set, recorded on cs before the first copy
 };
 
 // How the A1 products reach the rows the plan did not store (SrtRot).
@@ -100,6 +104,7 @@ int sink_copy(HostSink* hs, int chunk, cudaStream_t st, float* host, const float
               int64_t width_elems, int64_t pitch_elems, int64_t height) {
   SRT_CUDA_TRY(cudaEventRecord(hs->ev[chunk], st));
   SRT_CUDA_TRY(cudaStreamWaitEvent(hs->cs, hs->ev[chunk], 0));
+  if (chunk == 0 && hs->t0) SRT_CUDA_TRY(cudaEventRecord(hs->t0, hs->cs));
   SRT_CUDA_TRY(cudaMemcpy2DAsync(host, pitch_elems * 4, dev, pitch_elems * 4, width_elems * 4,
                                  height, cudaMemcpyDeviceToHost, hs->cs));
   return SRT_OK;
@@ -126,7 +131,7 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   // the same time gather a narrow band of Y1' rows, which stays in L2.  A
   // block owns 4 rings x 2 radii: neighbouring rings gather shifted copies
   // of the same cells (A2 is Toeplitz in z), so its warps share L1 lines.
-  const int nc = hs ? (g.n_zs < kHostChunks ? g.n_zs : kHostChunks) : 1;
+  const int nc = hs ? (g.n_zs < hs->chunks ? g.n_zs : hs->chunks) : 1;
   for (int c = 0; c < nc; ++c) {
     const int h0 = (int)((int64_t)g.n_zs * c / nc), h1 = (int)((int64_t)g.n_zs * (c + 1) / nc);
     const int64_t ra = (int64_t)h0 * g.n_ell, rn = (int64_t)(h1 - h0) * g.n_ell;
@@ -170,7 +175,7 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   if (!hs) mark(p, 1, 3, st);
   // rows (pixels) in blocks of 4 x 2 pixels: a circle crossing a compact
   // tile touches more of its pixels than of a line of 8, so warps share L1
-  const int nc = hs ? (g.ms < kHostChunks ? g.ms : kHostChunks) : 1;
+  const int nc = hs ? (g.ms < hs->chunks ? g.ms : hs->chunks) : 1;
   for (int c = 0; c < nc; ++c) {
     const int x0 = (int)((int64_t)g.ms * c / nc), x1 = (int)((int64_t)g.ms * (c + 1) / nc);
     const int64_t ra = (int64_t)x0 * g.ms, rn = (int64_t)(x1 - x0) * g.ms;
@@ -341,6 +346,190 @@ int srt_forward_host(srt_plan_t p, const float* f_host, float* p_host, int32_t b
 int srt_adjoint_host(srt_plan_t p, const float* p_host, float* f_host, int32_t batch, void* ws,
                      size_t ws_bytes, void* stream) {
   return host_call(p, 1, p_host, f_host, batch, ws, ws_bytes, stream);
+}
+
+// ------------------------------------------------------------ pipelines
+// Host-buffer calls with several in flight: two slots of device input and
+// output buffers, one stream each for input copies, computation and result
+// copies.  Call i copies its input into slot i % 2 while call i - 1 computes
+// on the other slot, and its result goes back while call i + 1 computes, so
+// a sequence of calls costs about the larger of the copy and the compute
+// time per call instead of their sum.  The compute stream runs the calls in
+// submission order, sharing one pair of intermediate buffers.
+}  // extern "C"
+
+struct srt_pipe_s {
+  // events of one call: input copy (h0, h1), transform (c0, c1), result copy
+  // (d0, d1); d1 marks the call complete.  Kept for the last kRing calls.
+  static constexpr int kRing = 8;
+  struct Call {
+    cudaEvent_t h0 = nullptr, h1 = nullptr, c0 = nullptr, c1 = nullptr, d0 = nullptr,
+                d1 = nullptr;
+  };
+  srt_plan_s* plan = nullptr;
+  int batch = 0;
+  void* mem = nullptr;
+  float* in[2] = {};
+  float* out[2] = {};
+  float* w0 = nullptr;
+  float* w1 = nullptr;
+  cudaStream_t cs = nullptr, h2d = nullptr, d2h = nullptr;
+  Call call[kRing];
+  cudaEvent_t chunk[kHostChunks] = {};
+  int64_t next = 0;       // tickets issued
+  int64_t done_upto = -1; // every call up to this ticket has completed
+};
+
+namespace {
+
+void pipe_free(srt_pipe_s* q) {
+  if (!q) return;
+  if (q->cs) cudaStreamSynchronize(q->cs);
+  if (q->h2d) cudaStreamSynchronize(q->h2d);
+  if (q->d2h) cudaStreamSynchronize(q->d2h);
+  for (auto& c : q->call)
+    for (cudaEvent_t e : {c.h0, c.h1, c.c0, c.c1, c.d0, c.d1})
+      if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : q->chunk)
+    if (e) cudaEventDestroy(e);
+  if (q->cs) cudaStreamDestroy(q->cs);
+  if (q->h2d) cudaStreamDestroy(q->h2d);
+  if (q->d2h) cudaStreamDestroy(q->d2h);
+  cudaFree(q->mem);
+  delete q;
+}
+
+}  // namespace
+
+extern "C" {
+
+int srt_pipe_create(srt_plan_t p, int32_t batch, srt_pipe_t* out) {
+  if (!out) return SRT_ERR_ARG;
+  *out = nullptr;
+  if (!p || batch <= 0) return SRT_ERR_ARG;
+  const srt_geometry& g = p->g;
+  const int64_t nf = (int64_t)batch * g.ms * g.ms * g.mz;
+  const int64_t np = (int64_t)batch * g.n_phi * g.n_zs * g.n_ell;
+  const int64_t io = align256((nf > np ? nf : np) * 4), buf = align256(buf_elems(g, batch) * 4);
+  srt_pipe_s* q = new (std::nothrow) srt_pipe_s();
+  if (!q) return SRT_ERR_OOM;
+  q->plan = p;
+  q->batch = batch;
+  cudaError_t e = cudaMalloc(&q->mem, (size_t)(4 * io + 2 * buf));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    q->mem = nullptr;
+    pipe_free(q);
+    return e == cudaErrorMemoryAllocation ? SRT_ERR_OOM : SRT_ERR_CUDA;
+  }
+  char* m = (char*)q->mem;
+  for (int s = 0; s < 2; ++s) {
+    q->in[s] = (float*)(m + (2 * s) * io);
+    q->out[s] = (float*)(m + (2 * s + 1) * io);
+  }
+  q->w0 = (float*)(m + 4 * io);
+  q->w1 = (float*)(m + 4 * io + buf);
+  bool ok = cudaStreamCreateWithFlags(&q->cs, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&q->h2d, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&q->d2h, cudaStreamNonBlocking) == cudaSuccess;
+  for (auto& c : q->call)
+    for (cudaEvent_t* ev : {&c.h0, &c.h1, &c.c0, &c.c1, &c.d0, &c.d1})
+      if (ok) ok = cudaEventCreate(ev) == cudaSuccess;
+  for (cudaEvent_t& ev : q->chunk)
+    if (ok) ok = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    pipe_free(q);
+    return SRT_ERR_CUDA;
+  }
+  *out = q;
+  return SRT_OK;
+}
+
+int srt_pipe_submit(srt_pipe_t q, int32_t direction, const float* in_host, float* out_host,
+                    int64_t* ticket) {
+  if (!q || !in_host || !out_host || (direction != 0 && direction != 1)) return SRT_ERR_ARG;
+  const srt_geometry& g = q->plan->g;
+  const int64_t nf = (int64_t)q->batch * g.ms * g.ms * g.mz;
+  const int64_t np = (int64_t)q->batch * g.n_phi * g.n_zs * g.n_ell;
+  const int64_t t = q->next;
+  const int s = (int)(t & 1);
+  srt_pipe_s::Call& c = q->call[t % srt_pipe_s::kRing];
+  if (t >= 2) {
+    // the slot's input is free once call t - 2 has consumed it, and its
+    // output once that call's result has reached the host
+    const srt_pipe_s::Call& pc = q->call[(t - 2) % srt_pipe_s::kRing];
+    SRT_CUDA_TRY(cudaStreamWaitEvent(q->h2d, pc.c1, 0));
+    SRT_CUDA_TRY(cudaStreamWaitEvent(q->cs, pc.d1, 0));
+  }
+  SRT_CUDA_TRY(cudaEventRecord(c.h0, q->h2d));
+  SRT_CUDA_TRY(cudaMemcpyAsync(q->in[s], in_host, (direction ? np : nf) * 4,
+                               cudaMemcpyHostToDevice, q->h2d));
+  SRT_CUDA_TRY(cudaEventRecord(c.h1, q->h2d));
+  SRT_CUDA_TRY(cudaStreamWaitEvent(q->cs, c.h1, 0));
+  SRT_CUDA_TRY(cudaEventRecord(c.c0, q->cs));
+  // one result copy after the transform: the next call's computation hides
+  // it, and the unchunked products keep their full launch width
+  HostSink hs;
+  hs.host = out_host;
+  hs.cs = q->d2h;
+  hs.chunks = 1;
+  hs.t0 = c.d0;
+  for (int k = 0; k < kHostChunks; ++k) hs.ev[k] = q->chunk[k];
+  if (direction == 0)
+    SRT_TRY(run_forward(q->plan, q->in[s], q->out[s], q->batch, q->w0, q->w1, q->cs, &hs));
+  else
+    SRT_TRY(run_adjoint(q->plan, q->in[s], q->out[s], q->batch, q->w0, q->w1, q->cs, &hs));
+  SRT_CUDA_TRY(cudaEventRecord(c.c1, q->cs));
+  SRT_CUDA_TRY(cudaEventRecord(c.d1, q->d2h));
+  if (ticket) *ticket = t;
+  ++q->next;
+  return SRT_OK;
+}
+
+int srt_pipe_stage_times(srt_pipe_t q, int64_t ticket, float* ms) {
+  constexpr int R = srt_pipe_s::kRing;
+  if (!q || !ms || ticket < 0 || ticket >= q->next) return SRT_ERR_ARG;
+  if (ticket < q->next - R) return SRT_ERR_NOT_READY;  // its events were reused
+  const srt_pipe_s::Call& c = q->call[ticket % R];
+  const cudaError_t e = cudaEventQuery(c.d1);
+  if (e == cudaErrorNotReady) return SRT_ERR_NOT_READY;
+  if (e != cudaSuccess) return SRT_ERR_CUDA;
+  SRT_CUDA_TRY(cudaEventElapsedTime(&ms[0], c.h0, c.h1));
+  SRT_CUDA_TRY(cudaEventElapsedTime(&ms[1], c.c0, c.c1));
+  SRT_CUDA_TRY(cudaEventElapsedTime(&ms[2], c.d0, c.d1));
+  // idle time of the compute stream before this call: from the end of the
+  // previous call's transform (0 for the first call)
+  ms[3] = 0.0f;
+  if (ticket > 0 && ticket - 1 >= q->next - R)
+    SRT_CUDA_TRY(cudaEventElapsedTime(&ms[3], q->call[(ticket - 1) % R].c1, c.c0));
+  return SRT_OK;
+}
+
+int srt_pipe_wait(srt_pipe_t q, int64_t ticket, double timeout_s) {
+  constexpr int R = srt_pipe_s::kRing;
+  if (!q || ticket < 0 || ticket >= q->next) return SRT_ERR_ARG;
+  if (ticket <= q->done_upto) return SRT_OK;
+  // the result copies run in submission order on one stream: an older call
+  // whose events were reused is complete once the oldest kept call is
+  const int64_t t = ticket < q->next - R ? q->next - R : ticket;
+  const cudaEvent_t ev = q->call[t % R].d1;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) {
+      if (t > q->done_upto) q->done_upto = t;
+      return SRT_OK;
+    }
+    if (e != cudaErrorNotReady) return SRT_ERR_CUDA;
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_s >= 0 && dt > timeout_s) return SRT_ERR_TIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+int srt_pipe_destroy(srt_pipe_t q) {
+  pipe_free(q);
+  return SRT_OK;
 }
 
 size_t srt_dot_workspace_bytes(void) { return (size_t)SRT_DOT_BLOCKS * sizeof(double); }

@@ -225,6 +225,62 @@ class Plan:
             pass
 
 
+class Pipeline:
+    """Host-buffer calls with up to two in flight (srt_pipe_*): call i copies
+    its input while call i - 1 computes, and returns its result in chunks
+    while call i + 1 starts.  submit() returns a ticket at once; the host
+    tensors are held until wait(ticket)."""
+
+    def __init__(self, plan: Plan, batch: int = 1):
+        self.plan, self.batch = plan, batch
+        self._lib = L.lib()
+        h = ctypes.c_void_p()
+        check(self._lib.srt_pipe_create(plan._h, batch, ctypes.byref(h)), "srt_pipe_create")
+        self._h = h
+        self._held = {}
+
+    def submit(self, direction: str, in_host: torch.Tensor, out_host: torch.Tensor) -> int:
+        g = self.plan.geom
+        d = {"forward": 0, "adjoint": 1}[direction]
+        shapes = (g.f_shape, g.p_shape) if d == 0 else (g.p_shape, g.f_shape)
+        for t, shp in zip((in_host, out_host), shapes):
+            if t.device.type != "cpu" or self.plan._batch(t, shp) != self.batch:
+                raise ValueError(f"expected a host tensor of {self.batch} x {shp}")
+        tk = ctypes.c_int64()
+        check(self._lib.srt_pipe_submit(self._h, d, _ptr(in_host), _ptr(out_host),
+                                        ctypes.byref(tk)), "srt_pipe_submit")
+        self._held[tk.value] = (in_host, out_host)
+        return tk.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> torch.Tensor:
+        """Block until call `ticket`'s result is in its host tensor; returns it."""
+        check(self._lib.srt_pipe_wait(self._h, ticket, timeout_s), "srt_pipe_wait")
+        for t in [t for t in self._held if t <= ticket]:
+            out = self._held.pop(t)[1]
+            if t == ticket:
+                return out
+        return None
+
+    def stage_times(self, ticket: int):
+        """(input copy, transform, result copy, compute idle before it) in ms
+        for a finished call among the last 8 submitted."""
+        buf = (ctypes.c_float * 4)()
+        check(self._lib.srt_pipe_stage_times(self._h, ticket, buf), "srt_pipe_stage_times")
+        return tuple(buf)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.srt_pipe_destroy(self._h)
+            self._h = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 _dot_ws = {}
 
 
