@@ -198,13 +198,22 @@ def dist_init():
 
 
 def reduce_max(x, world):
+    """Max of x over the ranks (NCCL on the GPUs, or gloo on the host)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(world, steps, batch, total_ms):
+    """Whole-job fwd+adj pairs per second: every rank (an independent
+    replica) processes steps x batch pairs, and the job lasts as long as the
+    slowest rank (total_ms, already the max over ranks)."""
+    return world * steps * batch / (total_ms / 1e3)
 
 
 def barrier(world):
@@ -372,7 +381,7 @@ def run_ours(args):
     plan.set_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = reduce_max(sum(step_ms), world)
-    value = world * args.steps * B / (total_ms / 1e3)
+    value = job_rate(world, args.steps, B, total_ms)
 
     # per-stage figures from the CUDA events recorded on the launch stream
     model = stage_model(geom, plan.info, B, args.weights)
