@@ -463,6 +463,43 @@ def probe_costs(geoms: dict, batches=(1, 16), reps: int = 10):
     return rows
 
 
+def copy_tail_probe(seconds: float, mib: int = 151, window_s: float = 10.0):
+    """Pinned host->device and device->host copies of `mib` MiB on two streams,
+    back to back with a 4 ms pause, for `seconds`; yields the median and p99
+    copy times (CUDA events) of each window.  On the GB300 machines used here
+    the medians stay flat while the p99 grows several-fold after about a
+    minute, whatever runs on the GPU."""
+    n = (mib << 20) // 4
+    h_in = torch.empty(n).pin_memory()
+    h_out = torch.empty(n).pin_memory()
+    d_a = torch.empty(n, device="cuda")
+    d_b = torch.empty(n, device="cuda")
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    t_start = time.perf_counter()
+    win, k = [], 1
+    while time.perf_counter() - t_start < seconds:
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        with torch.cuda.stream(sa):
+            e[0].record()
+            d_a.copy_(h_in, non_blocking=True)
+            e[1].record()
+        with torch.cuda.stream(sb):
+            e[2].record()
+            h_out.copy_(d_b, non_blocking=True)
+            e[3].record()
+        e[1].synchronize()
+        e[3].synchronize()
+        win.append((e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])))
+        time.sleep(0.004)
+        if time.perf_counter() - t_start >= k * window_s:
+            w = np.array(win)
+            p50, p99 = np.median(w, axis=0), np.percentile(w, 99, axis=0)
+            yield {"t_s": k * window_s, "copies": len(w),
+                   "h2d_ms_p50": float(p50[0]), "h2d_ms_p99": float(p99[0]),
+                   "d2h_ms_p50": float(p50[1]), "d2h_ms_p99": float(p99[1])}
+            win, k = [], k + 1
+
+
 def main(argv=None):
     import argparse
     import json
@@ -482,52 +519,89 @@ def main(argv=None):
     ap.add_argument("--streams", type=int, default=4)
     ap.add_argument("--edges", default="64,96,128,192")
     ap.add_argument("--baseline", action="store_true", help="also run unbatched, no graphs")
+    ap.add_argument("--weights", choices=["fp32", "bf16", "both"], default="fp32",
+                    help="entry type of the batched server's plans (both: one run each)")
+    ap.add_argument("--segments", type=int, default=6,
+                    help="arrival-window segments per rate; the modes alternate between them")
+    ap.add_argument("--copy-probe", type=float, default=0.0, metavar="SECONDS",
+                    help="only time pinned 151 MB host<->device copies for this long and "
+                         "print median / p99 per 10 s")
     ap.add_argument("--probe", action="store_true",
                     help="only print the device time per volume of every geometry and "
                          "direction at batch 1 and at --max-batch")
     a = ap.parse_args(argv)
     geoms = serving_geometries(tuple(int(x) for x in a.edges.split(",")))
-    if a.probe:
-        for row in probe_costs(geoms, (1, a.max_batch)):
+    if a.copy_probe > 0:
+        for row in copy_tail_probe(a.copy_probe):
             print(json.dumps(row), flush=True)
+        return
+    wdts = ["fp32", "bf16"] if a.weights == "both" else [a.weights]
+    if a.probe:
+        for w in wdts:
+            gw = {k: g.with_(weight_dtype=w) for k, g in geoms.items()}
+            for row in probe_costs(gw, (1, a.max_batch)):
+                print(json.dumps({**row, "weights": w}), flush=True)
         return
     payloads = make_payloads(geoms)
     rates = [float(x) for x in a.rates.split(",")]
-    modes = [("batched", dict(max_batch=a.max_batch, use_graphs=True, batching=True,
-                              batch_budget_s=a.batch_budget_ms / 1e3))]
+    batched = dict(max_batch=a.max_batch, use_graphs=True, batching=True,
+                   batch_budget_s=a.batch_budget_ms / 1e3)
+    modes = [("batched" if w == "fp32" else "batched_bf16", batched, w) for w in wdts]
     if a.baseline:
-        modes.append(("unbatched_fp32", dict(max_batch=1, use_graphs=False, batching=False)))
+        modes.append(("unbatched_fp32", dict(max_batch=1, use_graphs=False, batching=False),
+                      "fp32"))
     out = {"duration_s": a.duration, "max_requests": a.max_requests, "warmup_s": a.warmup_s,
            "batch_budget_ms": a.batch_budget_ms,
            "budget_gb": a.budget_gb, "geometries": sorted(geoms), "runs": []}
-    for name, kw in modes:
-        srv = Server(geoms, int(a.budget_gb * 2**30), n_streams=a.streams, **kw)
+    # Every mode's server stays resident, and each rate's arrival window is
+    # cut into segments that visit the modes in alternating order with the
+    # same seeded arrivals: host<->device copy tails on the box drift over a
+    # run (see copy_tail_probe), so modes measured one after the other would
+    # not see the same conditions.
+    budget = int(min(a.budget_gb, 240.0 / len(modes)) * 2**30)
+    servers = {}
+    for name, kw, w in modes:
+        gw = {k: g.with_(weight_dtype=w) for k, g in geoms.items()}
+        srv = Server(gw, budget, n_streams=a.streams, **kw)
         for k in geoms:  # plans up front: latencies measure serving, not plan builds
             srv._plan(k)
         poisson_run(srv, rates[-1], a.warmup_s, payloads, seed=99, drop_results=True,
                     max_requests=min(a.max_requests, 3000))
-        for rate in rates:
-            base = dict(srv.stats.__dict__)
-            base_hist = collections.Counter(srv.stats.batch_hist)
-            t0 = time.perf_counter()
-            reqs = poisson_run(srv, rate, a.duration, payloads, drop_results=True,
-                               max_requests=a.max_requests)
-            wall = time.perf_counter() - t0
-            ok = [r for r in reqs if r.error is None and not r.cancelled]
-            batches = srv.stats.batches - base["batches"]
-            hist = srv.stats.batch_hist - base_hist
-            arrivals = [r.t_arrival for r in reqs]
+        srv.done.clear()
+        servers[name] = srv
+    names = [m[0] for m in modes]
+    out["segments"] = a.segments
+    out["budget_gb_per_server"] = budget / 2**30
+    for rate in rates:
+        acc = {n: dict(reqs=[], wall=0.0, batches=0, hist=collections.Counter(), failed=0,
+                       evictions=0) for n in names}
+        for seg in range(a.segments):
+            for name in (names if seg % 2 == 0 else names[::-1]):
+                srv, ac = servers[name], acc[name]
+                base = dict(srv.stats.__dict__)
+                base_hist = collections.Counter(srv.stats.batch_hist)
+                t0 = time.perf_counter()
+                ac["reqs"] += poisson_run(srv, rate, a.duration / a.segments, payloads,
+                                          seed=3 + 1000 * seg, drop_results=True,
+                                          max_requests=max(1, a.max_requests // a.segments))
+                ac["wall"] += time.perf_counter() - t0
+                ac["batches"] += srv.stats.batches - base["batches"]
+                ac["hist"] += srv.stats.batch_hist - base_hist
+                ac["failed"] += srv.stats.failed - base["failed"]
+                ac["evictions"] += srv.stats.evictions - base["evictions"]
+                srv.done.clear()
+        for name in names:
+            ac, srv = acc[name], servers[name]
+            ok = [r for r in ac["reqs"] if r.error is None and not r.cancelled]
             out["runs"].append(dict(
-                mode=name, rate_per_s=rate, requests=len(reqs),
-                arrival_window_s=(max(arrivals) - min(arrivals)) if arrivals else 0.0,
-                wall_s=wall, throughput_rps=len(ok) / wall, **latency_summary(ok),
-                failed=srv.stats.failed - base["failed"], batches=batches,
-                mean_batch=len(ok) / max(1, batches),
-                batch_hist={int(k): int(v) for k, v in sorted(hist.items())},
-                evictions=srv.stats.evictions - base["evictions"],
-                hbm_used_gb=srv.used_bytes() / 2**30))
+                mode=name, rate_per_s=rate, requests=len(ac["reqs"]), wall_s=ac["wall"],
+                throughput_rps=len(ok) / ac["wall"], **latency_summary(ok),
+                failed=ac["failed"], batches=ac["batches"],
+                mean_batch=len(ok) / max(1, ac["batches"]),
+                batch_hist={int(k): int(v) for k, v in sorted(ac["hist"].items())},
+                evictions=ac["evictions"], hbm_used_gb=srv.used_bytes() / 2**30))
             print(json.dumps(out["runs"][-1]), flush=True)
-            srv.done.clear()
+    for srv in servers.values():
         srv.close()
     print(json.dumps(out))
 

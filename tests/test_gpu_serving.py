@@ -30,18 +30,20 @@ _ALONE = {}
 
 
 def _alone(Plan, geoms, r):
-    if r.key not in _ALONE:
-        _ALONE[r.key] = Plan(geoms[r.key])
-    plan = _ALONE[r.key]
+    k = (r.key, geoms[r.key].weight_dtype)
+    if k not in _ALONE:
+        _ALONE[k] = Plan(geoms[r.key])
+    plan = _ALONE[k]
     x = r.payload.cuda()
     out = plan.forward(x) if r.direction == "fwd" else plan.adjoint(x)
     return out.cpu()
 
 
-@pytest.mark.parametrize("graphs", [True, False])
-def test_results_in_the_mix_equal_results_alone(env, graphs):
+@pytest.mark.parametrize("graphs,wdt", [(True, "fp32"), (False, "fp32"), (True, "bf16")])
+def test_results_in_the_mix_equal_results_alone(env, graphs, wdt):
     import torch
     SV, Plan, geoms, payloads = env
+    geoms = {k: g.with_(weight_dtype=wdt) for k, g in geoms.items()}
     srv = SV.Server(geoms, budget_bytes=8 << 30, max_batch=16, n_streams=3, use_graphs=graphs)
     rng = np.random.default_rng(5)
     reqs = []
