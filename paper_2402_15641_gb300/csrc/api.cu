@@ -17,6 +17,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace {
@@ -73,6 +75,16 @@ int check_ws(srt_plan_s* p, int batch, const void* ws, size_t ws_bytes) {
   return SRT_OK;
 }
 
+// NVTX range over a scope (host-side: marks when each stage is enqueued, and
+// lets a profiler select launches by stage name).  Header-only NVTX3: a no-op
+// unless a tool is attached.
+struct NvRange {
+  explicit NvRange(const char* name) { nvtxRangePushA(name); }
+  ~NvRange() { nvtxRangePop(); }
+  NvRange(const NvRange&) = delete;
+  NvRange& operator=(const NvRange&) = delete;
+};
+
 // Destination of a host-buffer call: the result is copied to `host` in
 // chunks on the copy stream `cs` as the chunks are produced on the compute
 // stream, so the copies overlap the rest of the transform.
@@ -119,13 +131,20 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   const int64_t pix = (int64_t)g.ms * g.ms, r1 = (int64_t)g.n_phi * g.n_ell;
   const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
   const int64_t nb = (int64_t)B * g.n_phi;  // dense width of the second stage
+  NvRange all("srt forward (Algorithm 1)");
   if (!hs) mark(p, 0, 0, st);
   // Y1[b][j][l][k] = A1 F_b (CRT in the first plane, all slabs at once)
   // rows (j, l) visited radius-chunk-major across sensor columns (L2 reuse of F)
-  SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B, st,
-                   g.n_phi, g.n_ell, 1, 0, r1, a1_rot(p, 1)));
+  {
+    NvRange r("A1 product");
+    SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B,
+                     st, g.n_phi, g.n_ell, 1, 0, r1, a1_rot(p, 1)));
+  }
   if (!hs) mark(p, 0, 1, st);
-  SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
+  {
+    NvRange r("reshape P1");
+    SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
+  }
   if (!hs) mark(p, 0, 2, st);
   // rows (h, m) visited radius-chunk-major across rings: blocks running at
   // the same time gather a narrow band of Y1' rows, which stays in L2.  A
@@ -135,6 +154,7 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   for (int c = 0; c < nc; ++c) {
     const int h0 = (int)((int64_t)g.n_zs * c / nc), h1 = (int)((int64_t)g.n_zs * (c + 1) / nc);
     const int64_t ra = (int64_t)h0 * g.n_ell, rn = (int64_t)(h1 - h0) * g.n_ell;
+    NvRange r("A2 product + reshape P2");
     if (p->toeplitz)  // A2 from the taps of the master tensor
       SRT_TRY(srt_taps_apply(p, false, ra, rn, h1 - h0, g.n_ell, 4, w1, nb, w0 + ra * nb, nb,
                              (int)nb, st));
@@ -162,15 +182,25 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   const int64_t pix = (int64_t)g.ms * g.ms, r1 = (int64_t)g.n_phi * g.n_ell;
   const int64_t c1 = (int64_t)g.n_ell * g.mz, r2 = (int64_t)g.n_zs * g.n_ell;
   const int64_t nb = (int64_t)B * g.n_phi;
+  NvRange all("srt adjoint (Algorithm 2)");
   if (!hs) mark(p, 1, 0, st);
-  SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
+  {
+    NvRange r("reshape P2^-1");
+    SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
+  }
   if (!hs) mark(p, 1, 1, st);
-  if (p->toeplitz)  // A2^T from the taps of the master tensor
-    SRT_TRY(srt_taps_apply(p, true, 0, c1, 0, 0, 1, w0, nb, w1, nb, (int)nb, st));
-  else
-    SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));
+  {
+    NvRange r("A2^T product");
+    if (p->toeplitz)  // A2^T from the taps of the master tensor
+      SRT_TRY(srt_taps_apply(p, true, 0, c1, 0, 0, 1, w0, nb, w1, nb, (int)nb, st));
+    else
+      SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));
+  }
   if (!hs) mark(p, 1, 2, st);
-  SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
+  {
+    NvRange r("reshape P1^-1");
+    SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
+  }
   const float* f1 = w0;  // F1[b][j][l][k], input of A1^T
   if (!hs) mark(p, 1, 3, st);
   // rows (pixels) in blocks of 4 x 2 pixels: a circle crossing a compact
@@ -179,6 +209,7 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   for (int c = 0; c < nc; ++c) {
     const int x0 = (int)((int64_t)g.ms * c / nc), x1 = (int)((int64_t)g.ms * (c + 1) / nc);
     const int64_t ra = (int64_t)x0 * g.ms, rn = (int64_t)(x1 - x0) * g.ms;
+    NvRange r("A1^T product");
     SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f + ra * g.mz, g.mz,
                      pix * g.mz, g.mz, B, st, x1 - x0, g.ms, 4, ra, rn, a1_rot(p, 2)));
     if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra * g.mz, f + ra * g.mz, rn * g.mz, pix * g.mz, B));
