@@ -398,6 +398,7 @@ def run_ours(args):
             stages[f"{d}.{name}"] = s
     dom = max(stages, key=lambda k: stages[k]["ms"])
     ds = stages[dom]
+    delivery = 152 * 32 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     if "tflop_s" in ds:
         roof = {"bound": "alu", "achieved": ds["tflop_s"], "peak": round(pk["fp32_tflops"], 2),
                 "unit": "TFLOP/s", "frac": ds["fp32_frac"],
@@ -405,7 +406,11 @@ def run_ours(args):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock "
                                f"{pk['sm_max_mhz']:.0f} MHz",
                 "fma_measured_tflops": round(fma_meas, 2),
-                "frac_of_measured_fma": round(ds["tflop_s"] / fma_meas, 4)}
+                "frac_of_measured_fma": round(ds["tflop_s"] / fma_meas, 4),
+                # every FMA of a gathered product takes one gathered FP32
+                # operand; L1 returns 128 B (32 operands) per clock per SM
+                "delivery_roof_tflops": round(delivery, 2),
+                "frac_of_delivery_roof": round(ds["tflop_s"] / delivery, 4)}
     else:
         roof = {"bound": "hbm", "achieved": ds["gb_s"], "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ds["hbm_frac"], "traffic": ncu_traffic(dom, args.workload),
