@@ -240,6 +240,8 @@ class Pipeline:
         self._held = {}
 
     def submit(self, direction: str, in_host: torch.Tensor, out_host: torch.Tensor) -> int:
+        if not getattr(self, "_h", None) or not getattr(self.plan, "_h", None):
+            raise RuntimeError("pipeline or its plan has been closed")
         g = self.plan.geom
         d = {"forward": 0, "adjoint": 1}[direction]
         shapes = (g.f_shape, g.p_shape) if d == 0 else (g.p_shape, g.f_shape)

@@ -93,3 +93,10 @@ def test_pipeline_argument_errors(srt, orc):
     assert pipe.wait(t) is p
     assert float(p.abs().max()) == 0.0
     pipe.close()
+    with pytest.raises(RuntimeError):
+        pipe.submit("forward", f, p)            # closed pipeline
+    pipe2 = srt.Pipeline(plan, 1)
+    plan.close()
+    with pytest.raises(RuntimeError):
+        pipe2.submit("forward", f, p)           # its plan was closed
+    pipe2.close()
