@@ -181,21 +181,23 @@ int srt_adjoint_host(srt_plan_t plan, const float* p_host, float* f_host, int32_
 
 /*
  * Pipelined host-buffer calls: a sequence of forward and adjoint calls on
- * HOST buffers with up to two in flight, so that one call's input copy
- * overlaps the previous call's computation and its result copy (one copy,
- * after the transform) overlaps the next call's.  Results are bitwise those of srt_forward_host /
+ * HOST buffers with up to `slots` (2-4) in flight, so that a call's input
+ * copy overlaps earlier calls' computation and its result copy (one copy,
+ * after the transform) overlaps later calls'.  Results are bitwise those of srt_forward_host /
  * srt_adjoint_host.  (The paper has no counterpart; this is the serving-side
  * form of the host-buffer calls.)
- *   srt_pipe_create: device buffers for two calls of `batch` volumes (two
- *     input and two output slots of the larger of f and p, plus one
- *     transform workspace) and three streams of its own (input copies,
- *     computation, result copies).  Errors: SRT_ERR_ARG, SRT_ERR_OOM,
- *     SRT_ERR_CUDA; on error *pipe is set to NULL.
+ *   srt_pipe_create: device buffers for `slots` calls of `batch` volumes
+ *     (an input and an output buffer per slot, each the larger of f and p,
+ *     plus one transform workspace) and three streams of its own (input
+ *     copies, computation, result copies).  More slots give a slow copy
+ *     more time to finish before its call's transform is due.  Errors:
+ *     SRT_ERR_ARG (slots outside 2-4), SRT_ERR_OOM, SRT_ERR_CUDA; on error
+ *     *pipe is set to NULL.
  *   srt_pipe_submit: enqueue one call (direction 0 = forward, f_host ->
  *     p_host; 1 = adjoint, p_host -> f_host) and return without waiting;
  *     *ticket (may be NULL) numbers the calls 0, 1, 2, ...  Call i uses slot
- *     i % 2 and starts its input copy once call i - 2 has consumed that
- *     slot's input.  in_host and out_host must stay allocated and unchanged
+ *     i % slots and starts its input copy once call i - slots has consumed
+ *     that slot's input.  in_host and out_host must stay allocated and unchanged
  *     (out_host unread) until srt_pipe_wait(ticket) has returned SRT_OK;
  *     pinned memory gives full copy speed.  The calls run in submission
  *     order.  Errors: SRT_ERR_ARG (null pipe or buffer, bad direction),
@@ -214,7 +216,7 @@ int srt_adjoint_host(srt_plan_t plan, const float* p_host, float* f_host, int32_
  *     no-op).  Not thread safe: one host thread drives a pipe.
  */
 typedef struct srt_pipe_s* srt_pipe_t;
-int srt_pipe_create(srt_plan_t plan, int32_t batch, srt_pipe_t* pipe);
+int srt_pipe_create(srt_plan_t plan, int32_t batch, int32_t slots, srt_pipe_t* pipe);
 int srt_pipe_submit(srt_pipe_t pipe, int32_t direction, const float* in_host, float* out_host,
                     int64_t* ticket);
 int srt_pipe_wait(srt_pipe_t pipe, int64_t ticket, double timeout_s);

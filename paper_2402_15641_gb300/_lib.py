@@ -65,7 +65,7 @@ SIGNATURES = {
     "srt_stage_times": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(ctypes.c_float), _I32]),
     "srt_launches_per_call": (ctypes.c_int, [_VP, _I32, _I32]),
     "srt_fp32_fma_peak": (ctypes.c_int, [_I32, ctypes.POINTER(ctypes.c_double), _VP]),
-    "srt_pipe_create": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_VP)]),
+    "srt_pipe_create": (ctypes.c_int, [_VP, _I32, _I32, ctypes.POINTER(_VP)]),
     "srt_pipe_submit": (ctypes.c_int, [_VP, _I32, _VP, _VP, ctypes.POINTER(_I64)]),
     "srt_pipe_wait": (ctypes.c_int, [_VP, _I64, ctypes.c_double]),
     "srt_pipe_stage_times": (ctypes.c_int, [_VP, _I64, ctypes.POINTER(ctypes.c_float)]),

@@ -380,10 +380,10 @@ int srt_adjoint_host(srt_plan_t p, const float* p_host, float* f_host, int32_t b
 }
 
 // ------------------------------------------------------------ pipelines
-// Host-buffer calls with several in flight: two slots of device input and
+// Host-buffer calls with several in flight: 2-4 slots of device input and
 // output buffers, one stream each for input copies, computation and result
-// copies.  Call i copies its input into slot i % 2 while call i - 1 computes
-// on the other slot, and its result goes back while call i + 1 computes, so
+// copies.  Call i copies its input into slot i % slots while earlier calls
+// compute, and its result goes back while later calls compute, so
 // a sequence of calls costs about the larger of the copy and the compute
 // time per call instead of their sum.  The compute stream runs the calls in
 // submission order, sharing one pair of intermediate buffers.
@@ -397,11 +397,13 @@ struct srt_pipe_s {
     cudaEvent_t h0 = nullptr, h1 = nullptr, c0 = nullptr, c1 = nullptr, d0 = nullptr,
                 d1 = nullptr;
   };
+  static constexpr int kMaxSlots = 4;
   srt_plan_s* plan = nullptr;
   int batch = 0;
+  int slots = 2;
   void* mem = nullptr;
-  float* in[2] = {};
-  float* out[2] = {};
+  float* in[kMaxSlots] = {};
+  float* out[kMaxSlots] = {};
   float* w0 = nullptr;
   float* w1 = nullptr;
   cudaStream_t cs = nullptr, h2d = nullptr, d2h = nullptr;
@@ -434,10 +436,10 @@ void pipe_free(srt_pipe_s* q) {
 
 extern "C" {
 
-int srt_pipe_create(srt_plan_t p, int32_t batch, srt_pipe_t* out) {
+int srt_pipe_create(srt_plan_t p, int32_t batch, int32_t slots, srt_pipe_t* out) {
   if (!out) return SRT_ERR_ARG;
   *out = nullptr;
-  if (!p || batch <= 0) return SRT_ERR_ARG;
+  if (!p || batch <= 0 || slots < 2 || slots > srt_pipe_s::kMaxSlots) return SRT_ERR_ARG;
   const srt_geometry& g = p->g;
   const int64_t nf = (int64_t)batch * g.ms * g.ms * g.mz;
   const int64_t np = (int64_t)batch * g.n_phi * g.n_zs * g.n_ell;
@@ -446,7 +448,8 @@ int srt_pipe_create(srt_plan_t p, int32_t batch, srt_pipe_t* out) {
   if (!q) return SRT_ERR_OOM;
   q->plan = p;
   q->batch = batch;
-  cudaError_t e = cudaMalloc(&q->mem, (size_t)(4 * io + 2 * buf));
+  q->slots = slots;
+  cudaError_t e = cudaMalloc(&q->mem, (size_t)(2 * slots * io + 2 * buf));
   if (e != cudaSuccess) {
     cudaGetLastError();
     q->mem = nullptr;
@@ -454,12 +457,12 @@ int srt_pipe_create(srt_plan_t p, int32_t batch, srt_pipe_t* out) {
     return e == cudaErrorMemoryAllocation ? SRT_ERR_OOM : SRT_ERR_CUDA;
   }
   char* m = (char*)q->mem;
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < slots; ++s) {
     q->in[s] = (float*)(m + (2 * s) * io);
     q->out[s] = (float*)(m + (2 * s + 1) * io);
   }
-  q->w0 = (float*)(m + 4 * io);
-  q->w1 = (float*)(m + 4 * io + buf);
+  q->w0 = (float*)(m + 2 * slots * io);
+  q->w1 = (float*)(m + 2 * slots * io + buf);
   bool ok = cudaStreamCreateWithFlags(&q->cs, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&q->h2d, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&q->d2h, cudaStreamNonBlocking) == cudaSuccess;
@@ -483,12 +486,12 @@ int srt_pipe_submit(srt_pipe_t q, int32_t direction, const float* in_host, float
   const int64_t nf = (int64_t)q->batch * g.ms * g.ms * g.mz;
   const int64_t np = (int64_t)q->batch * g.n_phi * g.n_zs * g.n_ell;
   const int64_t t = q->next;
-  const int s = (int)(t & 1);
+  const int s = (int)(t % q->slots);
   srt_pipe_s::Call& c = q->call[t % srt_pipe_s::kRing];
-  if (t >= 2) {
-    // the slot's input is free once call t - 2 has consumed it, and its
+  if (t >= q->slots) {
+    // the slot's input is free once call t - slots has consumed it, and its
     // output once that call's result has reached the host
-    const srt_pipe_s::Call& pc = q->call[(t - 2) % srt_pipe_s::kRing];
+    const srt_pipe_s::Call& pc = q->call[(t - q->slots) % srt_pipe_s::kRing];
     SRT_CUDA_TRY(cudaStreamWaitEvent(q->h2d, pc.c1, 0));
     SRT_CUDA_TRY(cudaStreamWaitEvent(q->cs, pc.d1, 0));
   }

@@ -226,16 +226,17 @@ class Plan:
 
 
 class Pipeline:
-    """Host-buffer calls with up to two in flight (srt_pipe_*): call i copies
-    its input while call i - 1 computes, and returns its result in chunks
-    while call i + 1 starts.  submit() returns a ticket at once; the host
-    tensors are held until wait(ticket)."""
+    """Host-buffer calls with up to `slots` (2-4) in flight (srt_pipe_*): a
+    call copies its input while earlier calls compute, and its result goes
+    back while later calls compute.  submit() returns a ticket at once; the
+    host tensors are held until wait(ticket)."""
 
-    def __init__(self, plan: Plan, batch: int = 1):
-        self.plan, self.batch = plan, batch
+    def __init__(self, plan: Plan, batch: int = 1, slots: int = 3):
+        self.plan, self.batch, self.slots = plan, batch, slots
         self._lib = L.lib()
         h = ctypes.c_void_p()
-        check(self._lib.srt_pipe_create(plan._h, batch, ctypes.byref(h)), "srt_pipe_create")
+        check(self._lib.srt_pipe_create(plan._h, batch, slots, ctypes.byref(h)),
+              "srt_pipe_create")
         self._h = h
         self._held = {}
 

@@ -135,8 +135,8 @@ def test_null_arguments(L):
     assert lib.srt_dot_workspace_bytes() >= 8
     assert lib.srt_dot_f64(None, None, 1, None, None, 0, None) == L.SRT_ERR_ARG
     q = ctypes.c_void_p(1)
-    assert lib.srt_pipe_create(None, 1, ctypes.byref(q)) == L.SRT_ERR_ARG and not q.value
-    assert lib.srt_pipe_create(None, 1, None) == L.SRT_ERR_ARG
+    assert lib.srt_pipe_create(None, 1, 2, ctypes.byref(q)) == L.SRT_ERR_ARG and not q.value
+    assert lib.srt_pipe_create(None, 1, 2, None) == L.SRT_ERR_ARG
     tk = ctypes.c_int64()
     assert lib.srt_pipe_submit(None, 0, None, None, ctypes.byref(tk)) == L.SRT_ERR_ARG
     assert lib.srt_pipe_wait(None, 0, 1.0) == L.SRT_ERR_ARG

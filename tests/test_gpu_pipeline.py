@@ -19,14 +19,15 @@ def srt():
     return S
 
 
-@pytest.mark.parametrize("opts", [{}, {"csr_only": True}, {"a1_rotation": True},
-                                  {"weight_dtype": "bf16", "rho_linear": True}])
+@pytest.mark.parametrize("opts,slots", [({}, 2), ({}, 3), ({}, 4), ({"csr_only": True}, 3),
+                                        ({"a1_rotation": True}, 3),
+                                        ({"weight_dtype": "bf16", "rho_linear": True}, 2)])
 @pytest.mark.parametrize("batch", [1, 2])
-def test_pipeline_bitwise_equal_to_device_calls(srt, orc, opts, batch):
+def test_pipeline_bitwise_equal_to_device_calls(srt, orc, opts, slots, batch):
     import torch
     g, _ = geom_pair(orc, **dict(I.sizes("srt32")), **opts)
     plan = srt.Plan(g)
-    pipe = srt.Pipeline(plan, batch)
+    pipe = srt.Pipeline(plan, batch, slots=slots)
     rng = np.random.default_rng(23)
     dirs = ["forward", "adjoint", "forward", "forward", "adjoint", "adjoint", "forward"]
     calls = []
@@ -89,6 +90,9 @@ def test_pipeline_argument_errors(srt, orc):
         pipe.submit("forward", f.cuda(), p)     # device tensor
     with pytest.raises(srt.L.SrtError):
         pipe.wait(0)                            # nothing submitted yet
+    for bad in (1, 5):
+        with pytest.raises(srt.L.SrtError):
+            srt.Pipeline(plan, 1, slots=bad)    # slots outside 2-4
     t = pipe.submit("forward", f, p)
     assert pipe.wait(t) is p
     assert float(p.abs().max()) == 0.0
