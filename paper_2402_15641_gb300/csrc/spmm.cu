@@ -119,6 +119,11 @@ __global__ void __launch_bounds__(256) k_spmm_plain(int rows, const int32_t* __r
       v = wval<V>(val[eb + lane]);
     }
     const int cnt = min(32, e1 - eb);
+    // not unrolled: 31 registers, 64 resident warps per SM.  The products
+    // wait on their gathers, and more warps in flight beat the deeper
+    // per-warp schedule of an unrolled loop (40 registers, 48 warps): 4.5%
+    // faster, same summation order.
+#pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
       const int ci = __shfl_sync(FULL, c, i);
       const float vi = __shfl_sync(FULL, v, i);
@@ -188,7 +193,8 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
         v = wval<V>(val[eb + lane]);
       }
       const int cnt = min(32, e1 - eb);
-      for (int i = 0; i < cnt; ++i) {
+#pragma unroll 1
+      for (int i = 0; i < cnt; ++i) {  // not unrolled, as in k_spmm_plain
         const int ci = __shfl_sync(FULL, c, i);
         const float vi = __shfl_sync(FULL, v, i);
         const float* xr = x + (int64_t)ci * ldx;

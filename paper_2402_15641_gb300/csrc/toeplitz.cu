@@ -103,6 +103,10 @@ __global__ void __launch_bounds__(256) k_taps(TapArgs A, const V* __restrict__ v
       v = tap_w<V>(val[eb + lane]);
     }
     const int cnt = min(32, e1 - eb);
+    // not unrolled: 31 registers and 64 resident warps per SM against 48
+    // registers / 40 warps for the compiler's unroll; the product waits on
+    // its gathers, and more warps win (A2, A2^T 4.7% faster, same order)
+#pragma unroll 1
     for (int i = 0; i < cnt; ++i) {
       const int ci = __shfl_sync(FULL, c, i);
       const float vi = __shfl_sync(FULL, v, i);
