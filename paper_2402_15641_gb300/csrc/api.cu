@@ -204,14 +204,16 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   const float* f1 = w0;  // F1[b][j][l][k], input of A1^T
   if (!hs) mark(p, 1, 3, st);
   // rows (pixels) in blocks of 4 x 2 pixels: a circle crossing a compact
-  // tile touches more of its pixels than of a line of 8, so warps share L1
+  // tile touches more of its pixels than of a line of 8, so warps share L1;
+  // blocks walk 64 x 64 pixel super-tiles (where the grid divides), so the
+  // rows gathered at any time stay within what L2 holds (2% faster at 256^3)
   const int nc = hs ? (g.ms < hs->chunks ? g.ms : hs->chunks) : 1;
   for (int c = 0; c < nc; ++c) {
     const int x0 = (int)((int64_t)g.ms * c / nc), x1 = (int)((int64_t)g.ms * (c + 1) / nc);
     const int64_t ra = (int64_t)x0 * g.ms, rn = (int64_t)(x1 - x0) * g.ms;
     NvRange r("A1^T product");
     SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f + ra * g.mz, g.mz,
-                     pix * g.mz, g.mz, B, st, x1 - x0, g.ms, 4, ra, rn, a1_rot(p, 2)));
+                     pix * g.mz, g.mz, B, st, x1 - x0, g.ms, 4, ra, rn, a1_rot(p, 2), 64));
     if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra * g.mz, f + ra * g.mz, rn * g.mz, pix * g.mz, B));
   }
   if (hs) return SRT_OK;

@@ -99,9 +99,12 @@ struct SrtRot {
 // r0 <= r < r0 + rows (rows < 0: to A's end) and n < ncols.  With G > 0 the
 // launch's rows (G groups of R) are visited chunk-major across groups, a
 // block owning TG groups (1, 2, 4 or 8) x 8/TG consecutive rows of each.
+// With S > 0 (dividing G and R) the blocks walk S x S super-tiles of the
+// G x R row grid instead of chunk-major bands.
 int srt_spmm(const SrtCsr& A, int weight_dtype, const float* x, int64_t ldx, int64_t bsx, float* y,
              int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t stream, int G = 0,
-             int R = 0, int TG = 1, int64_t r0 = 0, int64_t rows = -1, SrtRot rot = SrtRot());
+             int R = 0, int TG = 1, int64_t r0 = 0, int64_t rows = -1, SrtRot rot = SrtRot(),
+             int S = 0);
 
 // out[b*obs + c*old + r] = in[b*ibs + r*ild + c] for r < rows, c < cols.
 int srt_transpose(const float* in, int64_t ild, int64_t ibs, float* out, int64_t old, int64_t obs,

@@ -52,11 +52,24 @@ __device__ __forceinline__ int rot_pixel(int p, int s, int ms, uint64_t magic) {
 // (chunk-major): all groups advance through i together, so the dense rows
 // gathered by concurrently running blocks stay within a narrow band of the
 // operand (L2 reuse), while a block's 8 warps gather overlapping rows (L1
-// reuse).  With G = 0 blocks take consecutive rows.
-__device__ __forceinline__ int block_row(int G, int R, int TG) {
+// reuse).  With G = 0 blocks take consecutive rows.  With S > 0 the G x R
+// grid is walked in S x S super-tiles (S dividing G and R), tiles row-major
+// inside each: the dense rows gathered by concurrently running blocks then
+// belong to a compact patch instead of a band across all G groups (A1^T:
+// pixels, whose circles through a 64 x 64 patch cover ~40% of the operand
+// instead of most of it).
+__device__ __forceinline__ int block_row(int G, int R, int TG, int S) {
   const int w = threadIdx.x >> 5;
   if (G <= 0) return blockIdx.x * (blockDim.x >> 5) + w;
   const int TI = 8 / TG;
+  if (S > 0) {
+    const int per_row = S / TG, bpt = per_row * (S / TI);
+    const int st = blockIdx.x / bpt, r = blockIdx.x - st * bpt;
+    const int nsx = G / S, sx = st % nsx, sy = st / nsx;
+    const int tx = r % per_row, ty = r / per_row;
+    const int g = sx * S + tx * TG + w / TI, i = sy * S + ty * TI + w % TI;
+    return (sy < R / S) ? g * R + i : -1;
+  }
   const int chunks = (R + TI - 1) / TI, tiles = (G + TG - 1) / TG;
   const int bid = blockIdx.x;
   const int c = bid / tiles, t = bid - c * tiles;
@@ -68,6 +81,7 @@ __device__ __forceinline__ int block_row(int G, int R, int TG) {
 struct Rows {
   int rows, r0;    // output rows of this launch, first output row
   int G, R, TG;    // block order
+  int S;           // super-tile side of the block order (0: chunk-major bands)
   SrtRot rot;
   uint64_t magic;  // ceil(2^40 / rot.ms)
 };
@@ -100,9 +114,9 @@ __global__ void __launch_bounds__(256) k_spmm_plain(int rows, const int32_t* __r
                                                     const float* __restrict__ x, int64_t ldx,
                                                     int64_t bsx, float* __restrict__ y,
                                                     int64_t ldy, int64_t bsy, int ncols, int G,
-                                                    int R, int TG) {
+                                                    int R, int TG, int S) {
   const int lane = threadIdx.x & 31;
-  const int row = block_row(G, R, TG);
+  const int row = block_row(G, R, TG, S);
   if (row < 0 || row >= rows) return;
   x += blockIdx.z * bsx;
   y += blockIdx.z * bsy;
@@ -162,9 +176,10 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
                                                   const float* __restrict__ x, int64_t ldx,
                                                   int64_t bsx, float* __restrict__ y, int64_t ldy,
                                                   int64_t bsy, int ncols, int G, int R, int TG,
-                                                  int ms, int n_ell, int q, uint64_t magic) {
+                                                  int S, int ms, int n_ell, int q,
+                                                  uint64_t magic) {
   const int lane = threadIdx.x & 31;
-  const int lr = block_row(G, R, TG);
+  const int lr = block_row(G, R, TG, S);
   if (lr < 0 || lr >= rows) return;
   const int row = r0 + lr;
   x += blockIdx.z * bsx;
@@ -277,18 +292,19 @@ int launch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t
   dim3 block(256);
   const bool vec = (ncols % 4 == 0) && (ldx % 4 == 0) && (ldy % 4 == 0) && (bsx % 4 == 0) &&
                    (bsy % 4 == 0) && ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0);
-  const int gx = W.G > 0 ? ((W.G + W.TG - 1) / W.TG) * ((W.R + 8 / W.TG - 1) / (8 / W.TG))
-                         : (W.rows + 7) / 8;
+  const int gx = W.S > 0   ? (W.G / W.S) * (W.R / W.S) * (W.S / W.TG) * (W.S / (8 / W.TG))
+                 : W.G > 0 ? ((W.G + W.TG - 1) / W.TG) * ((W.R + 8 / W.TG - 1) / (8 / W.TG))
+                           : (W.rows + 7) / 8;
   if (vec && MODE == 0) {
     const int32_t* rp = A.rowptr + W.r0;
     const int chunks = (ncols + 127) / 128;
     const int CH = chunks >= 4 ? 4 : chunks;
     dim3 grid(gx, CH == 4 ? (ncols + 511) / 512 : 1, batch);
     switch (CH) {
-      case 4: k_spmm_plain<V, 4><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG); break;
-      case 3: k_spmm_plain<V, 3><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG); break;
-      case 2: k_spmm_plain<V, 2><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG); break;
-      default: k_spmm_plain<V, 1><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG); break;
+      case 4: k_spmm_plain<V, 4><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S); break;
+      case 3: k_spmm_plain<V, 3><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S); break;
+      case 2: k_spmm_plain<V, 2><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S); break;
+      default: k_spmm_plain<V, 1><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S); break;
     }
   } else if (vec) {
     const int chunks = (ncols + 127) / 128;
@@ -298,7 +314,7 @@ int launch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t
 #define SRT_ROT_LAUNCH(C)                                                                     \
   k_spmm_rot<V, C, MODE><<<grid, block, 0, st>>>(W.rows, W.r0, A.rowptr, A.col, val, x, ldx, \
                                                  bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG,    \
-                                                 r.ms, r.n_ell, r.q, W.magic)
+                                                 W.S, r.ms, r.n_ell, r.q, W.magic)
     switch (CH) {
       case 4: SRT_ROT_LAUNCH(4); break;
       case 3: SRT_ROT_LAUNCH(3); break;
@@ -330,7 +346,7 @@ int dispatch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64
 
 int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx, float* y,
              int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t st, int G, int R,
-             int TG, int64_t r0, int64_t rows, SrtRot rot) {
+             int TG, int64_t r0, int64_t rows, SrtRot rot, int S) {
   if (rows < 0) rows = A.rows - r0;
   if (rows <= 0) return SRT_OK;
   if (rows > 0x7fffffff || r0 + rows > 0x7fffffff) return SRT_ERR_ARG;
@@ -343,7 +359,8 @@ int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx,
   }
   if (G > 0 && (int64_t)G * R != rows) G = 0;
   if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 1;
-  const Rows W{(int)rows, (int)r0, G, R, TG, rot, magic};
+  if (G <= 0 || S <= 0 || G % S || R % S || S % TG || S % (8 / TG)) S = 0;
+  const Rows W{(int)rows, (int)r0, G, R, TG, S, rot, magic};
   if (wdt == SRT_BF16) return dispatch<uint16_t>(A, A.v16, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
   return dispatch<float>(A, A.v32, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
 }
