@@ -245,6 +245,9 @@ int srt_pipe_destroy(srt_pipe_t pipe);
  */
 #define SRT_NOALLOC_WORKSPACE_BYTES (32u << 20)
 int srt_forward_noalloc(srt_plan_t plan, const float* f, float* p, int32_t batch, void* stream);
+/* The matched adjoint (as srt_adjoint) on the same scratch, with the same
+ * limits, errors and ordering rule. */
+int srt_adjoint_noalloc(srt_plan_t plan, const float* p, float* f, int32_t batch, void* stream);
 
 /*
  * FP64 inner product on the device: *out = sum_i (double)a[i] * (double)b[i],

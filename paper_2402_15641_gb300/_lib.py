@@ -57,6 +57,7 @@ SIGNATURES = {
     "srt_host_workspace_bytes": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_SZ)]),
     "srt_forward_host": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _SZ, _VP]),
     "srt_forward_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP]),
+    "srt_adjoint_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP]),
     "srt_adjoint_host": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _SZ, _VP]),
     "srt_dot_workspace_bytes": (_SZ, []),
     "srt_dot_f64": (ctypes.c_int, [_VP, _VP, _I64, _VP, _VP, _SZ, _VP]),

@@ -1,4 +1,5 @@
-// Forward transform for callers that cannot allocate device memory.
+// Forward and adjoint transforms for callers that cannot allocate device
+// memory.
 //
 // srt_forward needs a caller-provided device workspace for the intermediates
 // of the two stages.  Some callers have no way to provide one: code running
@@ -20,7 +21,8 @@
 
 namespace {
 
-// Scratch for srt_forward_noalloc (SRT_NOALLOC_WORKSPACE_BYTES per GPU).
+// Scratch for srt_forward_noalloc / srt_adjoint_noalloc
+// (SRT_NOALLOC_WORKSPACE_BYTES per GPU).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SRT_NOALLOC_WORKSPACE_BYTES];
 
 constexpr int kMaxDevices = 64;
@@ -47,18 +49,31 @@ int scratch_on_current_device(void** out) {
   return SRT_OK;
 }
 
-}  // namespace
-
-extern "C" int srt_forward_noalloc(srt_plan_t plan, const float* f, float* p, int32_t batch,
-                                   void* stream) {
-  if (!plan || !f || !p || batch <= 0) return SRT_ERR_ARG;
+// The scratch of the current device for a call of `batch` volumes on `plan`.
+int noalloc_scratch(srt_plan_t plan, int32_t batch, void** scratch) {
   int dev = -1;
   SRT_CUDA_TRY(cudaGetDevice(&dev));
   if (dev != plan->device) return SRT_ERR_ARG;  // the plan lives on another GPU
   size_t need = 0;
   SRT_TRY(srt_workspace_bytes(plan, batch, &need));
   if (need > (size_t)SRT_NOALLOC_WORKSPACE_BYTES) return SRT_ERR_WORKSPACE;
+  return scratch_on_current_device(scratch);
+}
+
+}  // namespace
+
+extern "C" int srt_forward_noalloc(srt_plan_t plan, const float* f, float* p, int32_t batch,
+                                   void* stream) {
+  if (!plan || !f || !p || batch <= 0) return SRT_ERR_ARG;
   void* scratch = nullptr;
-  SRT_TRY(scratch_on_current_device(&scratch));
+  SRT_TRY(noalloc_scratch(plan, batch, &scratch));
   return srt_forward(plan, f, p, batch, scratch, (size_t)SRT_NOALLOC_WORKSPACE_BYTES, stream);
+}
+
+extern "C" int srt_adjoint_noalloc(srt_plan_t plan, const float* p, float* f, int32_t batch,
+                                   void* stream) {
+  if (!plan || !p || !f || batch <= 0) return SRT_ERR_ARG;
+  void* scratch = nullptr;
+  SRT_TRY(noalloc_scratch(plan, batch, &scratch));
+  return srt_adjoint(plan, p, f, batch, scratch, (size_t)SRT_NOALLOC_WORKSPACE_BYTES, stream);
 }

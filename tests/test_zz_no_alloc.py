@@ -1,4 +1,4 @@
-"""srt_forward_noalloc: the forward transform for callers that cannot allocate
+"""srt_forward_noalloc / srt_adjoint_noalloc: the transforms for callers that cannot allocate
 device memory (their device memory belongs to another allocator, or they run
 where an allocation is not allowed or too slow).  It uses scratch the library
 keeps on each GPU instead of a caller workspace.
@@ -46,6 +46,15 @@ def test_noalloc_forward_matches_forward_twice():
         torch.cuda.synchronize()
         assert torch.isfinite(got).all()
         assert _rel(got, want) <= FP32_TOL, call
+        y = torch.from_numpy(rng.standard_normal((2, *plan.geom.p_shape)).astype(np.float32)).cuda()
+        want_a = plan.adjoint(y)
+        got_a = torch.full_like(want_a, float("nan"))
+        rc = lib.srt_adjoint_noalloc(plan._h, y.data_ptr(), got_a.data_ptr(), 2,
+                                     ctypes.c_void_p(stream.cuda_stream))
+        assert rc == _lib.SRT_OK, (call, rc)
+        torch.cuda.synchronize()
+        assert torch.isfinite(got_a).all()
+        assert _rel(got_a, want_a) <= FP32_TOL, call
 
 
 def test_noalloc_refuses_problems_larger_than_its_scratch():
@@ -62,3 +71,7 @@ def test_noalloc_refuses_problems_larger_than_its_scratch():
                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == _lib.SRT_ERR_WORKSPACE
     assert lib.srt_forward_noalloc(None, f.data_ptr(), p.data_ptr(), 1, None) == _lib.SRT_ERR_ARG
+    rc = lib.srt_adjoint_noalloc(plan._h, p.data_ptr(), f.data_ptr(), 1,
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == _lib.SRT_ERR_WORKSPACE
+    assert lib.srt_adjoint_noalloc(None, p.data_ptr(), f.data_ptr(), 1, None) == _lib.SRT_ERR_ARG
