@@ -471,12 +471,19 @@ def run_ours(args):
             prev = cur
         read(args.e2e_steps - 1, prev)
         e2e_s = reduce_max(time.perf_counter() - t0, world)
+        # the pipe's own events for its last calls: copies, transform, and
+        # the compute stream's idle time before each transform
+        last = prev[-1]
+        st = [pipe.stage_times(t) for t in range(max(0, last - 7), last + 1)]
+        pipe_ms = {k: round(float(np.mean([x[i] for x in st])), 3)
+                   for i, k in enumerate(("h2d", "transform", "d2h", "compute_idle"))}
         pipe.close()
         e2e = {"value": world * args.e2e_steps * B / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": f_h.numel() * 4 + y_h.numel() * 4,
                "d2h_bytes_per_step": p_h.numel() * 4 + a_h.numel() * 4,
                "steps": args.e2e_steps,
                "api": "srt_pipe_submit / srt_pipe_wait, 3 slots (calls in flight)",
+               "pipe_ms_per_call_last8": pipe_ms,
                "one_call_at_a_time": world * args.e2e_steps * B / serial_s}
 
     launches = args.steps * (plan.launches_per_call(0, B) + plan.launches_per_call(1, B))
