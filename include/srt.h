@@ -51,8 +51,9 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
 /* SRT_A1_ROTATION: with n_phi a multiple of 4 (and ms < 4096), store A1 and
  * A1^T for the first n_phi/4 sensor columns only: column j + n_phi/4 sees the
  * pixel grid turned by 90 degrees, A1[(j + n_phi/4, l), rot(p)] = A1[(j, l), p]
- * with rot(ix, iy) = (ms-1-iy, ix).  A1's memory drops 4x; the A1 product is
- * ~3% and the A1^T product ~11% slower at 256^3 (srt_plan_info_t.a1_rot). */
+ * with rot(ix, iy) = (ms-1-iy, ix).  A1's memory drops 4x, at the speed of
+ * the stored form (within 0.5% at 256^3; srt_plan_info_t.a1_rot reports it).
+ * Ignored where n_phi % 4 != 0 or ms >= 4096. */
 #define SRT_A1_ROTATION 0x8
 /* SRT_RHO_LINEAR: the intermediate f^{1,2} is piecewise linear in rho instead
  * of constant on the radius bins (Sec. 3.1 notes the method carries over to
