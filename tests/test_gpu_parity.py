@@ -297,6 +297,21 @@ def test_toeplitz_second_stage(srt, orc, sz, wdt):
     assert abs(lhs - rhs) / nrm <= ADJ_TOL
 
 
+def test_rings_off_the_slab_centres_use_csr(srt, orc):
+    """As many rings as slabs but shifted by 0.3 slab: A2 is not Toeplitz in
+    the slab index, so the plan must store it as CSR, and still match."""
+    sz = dict(ms=10, mz=8, dxy=0.5, dz=0.5, radius=6.0, n_phi=8, n_zs=8, n_ell=21,
+              zs=(-2.0 + 0.15, 2.0 + 0.15))
+    g, o = geom_pair(orc, **sz)
+    plan = srt.Plan(g)
+    assert plan.info["a2_taps"] == 0 and plan.info["n_taps"] == 0
+    rng = np.random.default_rng(31)
+    f = rng.uniform(0, 1, g.f_shape)
+    y = rng.standard_normal(g.p_shape)
+    assert rel_l2(to_np(plan.forward(to_dev(f))), orc.forward(o, f)) <= FP32_TOL
+    assert rel_l2(to_np(plan.adjoint(to_dev(y))), orc.adjoint(o, y)) <= FP32_TOL
+
+
 def test_plan_info_and_timing(srt, orc):
     import torch
     g, _ = geom_pair(orc, **dict(I.sizes("srt32")))
