@@ -298,8 +298,9 @@ def test_toeplitz_second_stage(srt, orc, sz, wdt):
 
 
 def test_rings_off_the_slab_centres_use_csr(srt, orc):
-    """As many rings as slabs but shifted by 0.3 slab: A2 is not Toeplitz in
-    the slab index, so the plan must store it as CSR, and still match."""
+    """As many rings as slabs but shifted by 0.3 slab: the master tensor of
+    the taps is assembled for rings at the slab centres, so the plan must
+    store A2 as CSR here, and still match the oracle."""
     sz = dict(ms=10, mz=8, dxy=0.5, dz=0.5, radius=6.0, n_phi=8, n_zs=8, n_ell=21,
               zs=(-2.0 + 0.15, 2.0 + 0.15))
     g, o = geom_pair(orc, **sz)
