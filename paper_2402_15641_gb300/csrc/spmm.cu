@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) k_spmm_plain(int rows, const int32_t* __r
       for (int q = 0; q < CH; ++q) {
         const int n = n0 + q * 128;
         if (n < ncols) {
-          const float4 xv = __ldg(reinterpret_cast<const float4*>(xr + n));
+          const float4 xv = srt_ldg_keep(xr + n);
           acc[q].x = fmaf(vi, xv.x, acc[q].x);
           acc[q].y = fmaf(vi, xv.y, acc[q].y);
           acc[q].z = fmaf(vi, xv.z, acc[q].z);
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
         for (int k = 0; k < CH; ++k) {
           const int n = n0 + k * 128;
           if (n < ncols) {
-            const float4 xv = __ldg(reinterpret_cast<const float4*>(xr + n));
+            const float4 xv = srt_ldg_keep(xr + n);
             acc[k].x = fmaf(vi, xv.x, acc[k].x);
             acc[k].y = fmaf(vi, xv.y, acc[k].y);
             acc[k].z = fmaf(vi, xv.z, acc[k].z);

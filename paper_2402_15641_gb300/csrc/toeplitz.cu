@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) k_taps(TapArgs A, const V* __restrict__ v
       for (int q = 0; q < CH; ++q) {
         const int n = n0 + q * 128;
         if (n < ncols) {
-          const float4 xv = __ldg(reinterpret_cast<const float4*>(xr + n));
+          const float4 xv = srt_ldg_keep(xr + n);
           acc[q].x = fmaf(vi, xv.x, acc[q].x);
           acc[q].y = fmaf(vi, xv.y, acc[q].y);
           acc[q].z = fmaf(vi, xv.z, acc[q].z);
