@@ -230,11 +230,12 @@ __global__ void __launch_bounds__(256) k_assemble(GeomDev G, int rows, int pass,
   }
 }
 
-// Expand the master tensor T (one ring at z = 0 on a doubled slab grid: rows m,
-// columns l*(2 mz - 1) + k2, offset d = k2 - (mz - 1)) into A2's rows (h, m):
-// entry (l, h + d) when 0 <= h + d < mz.  One warp per row; order and values
-// are kept, so A2 holds T's entries bitwise.
-__global__ void __launch_bounds__(256) k_expand_toeplitz(int mz, int n_ell, int rows, int pass,
+// Expand the master tensor T (one ring over D = mz + n_zs - 1 slab offsets:
+// rows m, columns l*D + q) into A2's rows (h, m): entry (l, k) with slab
+// k = h + q - (n_zs - 1) when 0 <= k < mz.  One warp per row; order and
+// values are kept, so A2 holds T's entries bitwise.
+__global__ void __launch_bounds__(256) k_expand_toeplitz(int mz, int n_zs, int n_ell, int rows,
+                                                         int pass,
                                                          const int32_t* __restrict__ tptr,
                                                          const int32_t* __restrict__ tcol,
                                                          const float* __restrict__ t32,
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(256) k_expand_toeplitz(int mz, int n_ell, int 
   const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
   if (row >= rows) return;
   const int h = row / n_ell, m = row % n_ell;
-  const int mz2 = 2 * mz - 1;
+  const int D = mz + n_zs - 1;
   const int e0 = tptr[m], e1 = tptr[m + 1];
   int total = 0;
   const int64_t base = pass ? rowptr[row] : 0;
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(256) k_expand_toeplitz(int mz, int n_ell, int 
     int c = 0;
     if (e < e1) {
       const int cc = tcol[e];
-      const int l = cc / mz2, k = h + (cc % mz2) - (mz - 1);
+      const int l = cc / D, k = h + (cc % D) - (n_zs - 1);
       keep = k >= 0 && k < mz;
       c = l * mz + k;
     }
@@ -510,13 +511,13 @@ void srt_csr_free(SrtCsr* m) {
   *m = SrtCsr();
 }
 
-// The rings coincide with the slab centres: n_zs = mz and the ring range is
-// the volume height (to rounding).
+// The rings are spaced like the slabs (ring spacing = dz to rounding), so A2
+// is Toeplitz in the slab offset whatever the number of rings and their
+// offset from the slab centres.
 static bool toeplitz_applies(const srt_geometry& g) {
-  const double h = g.mz * g.dz;
-  return g.n_zs == g.mz && fabs(g.zs_lo + 0.5 * h) <= 1e-12 * h &&
-         fabs(g.zs_hi - 0.5 * h) <= 1e-12 * h && !(g.flags & SRT_CSR_ONLY) && g.n_ell <= 0xffff &&
-         2 * g.mz - 1 <= 0x7fff;
+  const double spacing = (g.zs_hi - g.zs_lo) / g.n_zs;
+  return fabs(spacing - g.dz) <= 1e-12 * g.dz && !(g.flags & SRT_CSR_ONLY) &&
+         g.n_ell <= 0xffff && (int64_t)g.mz + g.n_zs - 1 <= 0x7fff;
 }
 
 static int expand_toeplitz(const SrtCsr& T, const srt_geometry& g, SrtCsr* a2, int64_t* bytes,
@@ -531,9 +532,9 @@ static int expand_toeplitz(const SrtCsr& T, const srt_geometry& g, SrtCsr* a2, i
   SRT_TRY(tmp.get(&dtot, 1));
   SRT_TRY(srt_dmalloc(&a2->rowptr, (int64_t)rows + 1, bytes));
   const int blocks = (int)(((int64_t)rows * 32 + 255) / 256);
-  k_expand_toeplitz<<<blocks, 256, 0, st>>>(g.mz, g.n_ell, rows, 0, T.rowptr, T.col, T.v32, T.v16,
-                                            T.v64, counts, nullptr, nullptr, nullptr, nullptr,
-                                            nullptr);
+  k_expand_toeplitz<<<blocks, 256, 0, st>>>(g.mz, g.n_zs, g.n_ell, rows, 0, T.rowptr, T.col,
+                                            T.v32, T.v16, T.v64, counts, nullptr, nullptr,
+                                            nullptr, nullptr, nullptr);
   SRT_CUDA_TRY(cudaGetLastError());
   int64_t nnz = 0;
   SRT_TRY(srt_scan_counts(counts, a2->rowptr, rows, dtot, &nnz, st));
@@ -543,9 +544,9 @@ static int expand_toeplitz(const SrtCsr& T, const srt_geometry& g, SrtCsr* a2, i
   if (T.v32) SRT_TRY(srt_dmalloc(&a2->v32, nnz, bytes));
   if (T.v16) SRT_TRY(srt_dmalloc(&a2->v16, nnz, bytes));
   if (T.v64) SRT_TRY(srt_dmalloc(&a2->v64, nnz, nullptr));
-  k_expand_toeplitz<<<blocks, 256, 0, st>>>(g.mz, g.n_ell, rows, 1, T.rowptr, T.col, T.v32, T.v16,
-                                            T.v64, nullptr, a2->rowptr, a2->col, a2->v32, a2->v16,
-                                            a2->v64);
+  k_expand_toeplitz<<<blocks, 256, 0, st>>>(g.mz, g.n_zs, g.n_ell, rows, 1, T.rowptr, T.col,
+                                            T.v32, T.v16, T.v64, nullptr, a2->rowptr, a2->col,
+                                            a2->v32, a2->v16, a2->v64);
   SRT_CUDA_TRY(cudaGetLastError());
   SRT_CUDA_TRY(cudaStreamSynchronize(st));
   return SRT_OK;
@@ -568,13 +569,21 @@ int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
   plan->nnz1 = plan->a1.nnz * copies;
   plan->dropped1 *= copies;
   if (toeplitz_applies(plan->g)) {
-    // master tensor: one ring at z = 0 over 2 mz - 1 slabs centred on it;
-    // A2 and A2^T are applied from its taps and never stored as matrices
+    // master tensor: one ring over D = mz + n_zs - 1 slabs, slab q at offset
+    // d = q + dmin from it, dmin = -(n_zs - 1) - s, where the ring range
+    // starts s dz + eps above the volume's bottom (s the nearest integer);
+    // the ring sits eps above its slab's centre, as every ring does.  A2 and
+    // A2^T are applied from its taps and never stored as matrices.
+    const int D = G.mz + G.n_zs - 1;
+    const double delta = G.zs_lo + G.hz;
+    const double sh = nearbyint(delta / G.dz), eps = delta - sh * G.dz;
+    const double dmin = -(G.n_zs - 1) - sh;
+    const double zr = eps - dmin * G.dz - 0.5 * D * G.dz + 0.5 * G.dz;
     GeomDev GT = G;
-    GT.mz = 2 * G.mz - 1;
+    GT.mz = D;
     GT.n_zs = 1;
-    GT.zs_lo = -0.5 * G.dz;
-    GT.zs_hi = 0.5 * G.dz;
+    GT.zs_lo = zr - 0.5 * G.dz;
+    GT.zs_hi = zr + 0.5 * G.dz;
     GT.hz = 0.5 * GT.mz * GT.dz;
     SRT_TRY(assemble_one<false>(GT, wdt, &plan->tm, &plan->dropped2, &plan->bytes, st));
     int64_t nnz2 = 0;

@@ -1,24 +1,29 @@
 // Second product of Algorithms 1 and 2 through the Toeplitz structure of A2.
 //
-// When the sensor rings sit at the slab centres (n_zs = mz over the volume
-// height), the semicircle of ring h and radius l_m meets cell (radius bin l,
-// slab k) exactly as the semicircle of ring h+1 meets cell (l, k+1):
-//   A2[(h,m),(l,k)] = T[m, d = k - h, l],
+// When the sensor rings are spaced like the slabs (ring spacing dz, any
+// number n_zs of rings, any offset), ring h sits at slab h + s plus a fixed
+// fraction eps of a slab (offset of the ring range = s dz + eps), and the
+// semicircle of ring h and radius l_m meets cell (radius bin l, slab k)
+// exactly as the semicircle of ring h+1 meets cell (l, k+1):
+//   A2[(h,m),(l,k)] = T[m, d = k - h - s, l],
 // so all of A2 (and A2^T) is held by the master tensor T: a few "taps"
-// (l, d, weight) per radius m instead of one row per (ring, radius).
+// (l, d, weight) per radius m instead of one row per (ring, radius).  T is
+// assembled once for one ring at eps over the D = mz + n_zs - 1 slab offsets
+// d = q - (n_zs - 1) - s, q < D, that some (ring, slab) pair takes.
 //
 // The taps are stored twice, grouped so that the entries of any output row
 // form ONE contiguous range, which the product kernel then walks exactly like
 // a CSR row (coalesced batch of 32 entries, shuffle broadcast, float4
 // gathers of dense rows):
-//   forward  (rows (h, m) of A2):   sub-rows (m, q = d + mz - 1), each listing
-//     l ascending; row (h, m) is sub-rows q = mz-1-h .. 2mz-2-h, i.e. every
-//     offset d with 0 <= h + d < mz.  Entry key = l | q << 16; gathered row
-//     l*mz + h + d.
-//   adjoint (rows (l, k) of A2^T):  sub-rows (l, e = mz - 1 - d), each listing
-//     m ascending; row (l, k) is sub-rows e = mz-1-k .. 2mz-2-k, i.e. rings
-//     h = k - d = 0 .. mz-1 in ascending order.  Entry key = m | e << 16;
-//     gathered row h*n_ell + m.
+//   forward  (rows (h, m) of A2):   sub-rows (m, q), each listing l
+//     ascending; row (h, m) is sub-rows q = n_zs-1-h .. n_zs-2-h+mz, i.e.
+//     every slab k = h + q - (n_zs-1) of the volume.  Entry key = l | q << 16;
+//     gathered row l*mz + k.
+//   adjoint (rows (l, k) of A2^T):  sub-rows (l, e = D - 1 - q), each listing
+//     m ascending; row (l, k) is sub-rows e = mz-1-k .. mz-2-k+n_zs, i.e.
+//     rings h = k + e - (mz-1) = 0 .. n_zs-1 in ascending order.  Entry key =
+//     m | e << 16; gathered row h*n_ell + m.
+// With the rings at the slab centres (n_zs = mz, s = eps = 0), D = 2 mz - 1.
 // The adjoint visits its entries in the same order as the CSR form of A2^T
 // (ascending (h, m)), the forward by ascending (d, l).  Every output row is
 // owned by one warp: no atomics.
@@ -47,7 +52,7 @@ __device__ __forceinline__ float tap_w<uint16_t>(uint16_t v) {
 struct TapArgs {
   const int32_t* rowptr;  // sub-row pointers
   const int32_t* key;     // packed (index, offset) per tap
-  int mz, n_ell, r0;      // r0: first output row of this launch
+  int mz, n_zs, n_ell, r0;  // r0: first output row of this launch
   int rows, G, R, TG;     // rows of this launch; block order (G groups of R, TG per block)
 };
 
@@ -75,7 +80,7 @@ __global__ void __launch_bounds__(256) k_taps(TapArgs A, const V* __restrict__ v
   const int lr = tap_row(A.G, A.R, A.TG);
   if (lr < 0 || lr >= A.rows) return;
   const int row = A.r0 + lr;
-  const int mz = A.mz, D = 2 * mz - 1;
+  const int mz = A.mz, nz = A.n_zs, D = mz + nz - 1;
   int a, b;  // (h, m) forward, (l, k) adjoint
   if (ADJ) {
     a = row / mz;
@@ -84,9 +89,9 @@ __global__ void __launch_bounds__(256) k_taps(TapArgs A, const V* __restrict__ v
     a = row / A.n_ell;
     b = row - a * A.n_ell;
   }
-  // forward: sub-rows m*D + (mz-1-h) .. +mz; adjoint: l*D + (mz-1-k) .. +mz
-  const int64_t s0 = ADJ ? (int64_t)a * D + (mz - 1 - b) : (int64_t)b * D + (mz - 1 - a);
-  const int e0 = A.rowptr[s0], e1 = A.rowptr[s0 + mz];
+  // forward: sub-rows m*D + (nz-1-h) .. +mz; adjoint: l*D + (mz-1-k) .. +nz
+  const int64_t s0 = ADJ ? (int64_t)a * D + (mz - 1 - b) : (int64_t)b * D + (nz - 1 - a);
+  const int e0 = A.rowptr[s0], e1 = A.rowptr[s0 + (ADJ ? nz : mz)];
   const int n0 = blockIdx.y * (128 * CH) + lane * 4;
   float4 acc[CH];
 #pragma unroll
@@ -97,9 +102,9 @@ __global__ void __launch_bounds__(256) k_taps(TapArgs A, const V* __restrict__ v
     if (eb + lane < e1) {
       const int kk = A.key[eb + lane];
       const int lo = kk & 0xffff, off = kk >> 16;
-      // forward: off = q, gathered row l*mz + h + q - (mz-1)
+      // forward: off = q, gathered row l*mz + h + q - (nz-1)
       // adjoint: off = e, h = k + e - (mz-1), gathered row h*n_ell + m
-      c = ADJ ? (b + off - (mz - 1)) * A.n_ell + lo : lo * mz + a + off - (mz - 1);
+      c = ADJ ? (b + off - (mz - 1)) * A.n_ell + lo : lo * mz + a + off - (nz - 1);
       v = tap_w<V>(val[eb + lane]);
     }
     const int cnt = min(32, e1 - eb);
@@ -142,11 +147,11 @@ __global__ void __launch_bounds__(256) k_taps_scalar(TapArgs A, const V* __restr
   const int lr = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (lr >= A.rows) return;
   const int row = A.r0 + lr;
-  const int mz = A.mz, D = 2 * mz - 1;
+  const int mz = A.mz, nz = A.n_zs, D = mz + nz - 1;
   const int a = ADJ ? row / mz : row / A.n_ell;
   const int b = ADJ ? row - a * mz : row - a * A.n_ell;
-  const int64_t s0 = ADJ ? (int64_t)a * D + (mz - 1 - b) : (int64_t)b * D + (mz - 1 - a);
-  const int e0 = A.rowptr[s0], e1 = A.rowptr[s0 + mz];
+  const int64_t s0 = ADJ ? (int64_t)a * D + (mz - 1 - b) : (int64_t)b * D + (nz - 1 - a);
+  const int e0 = A.rowptr[s0], e1 = A.rowptr[s0 + (ADJ ? nz : mz)];
   const int n0 = blockIdx.y * (32 * PER) + lane;
   float acc[PER];
 #pragma unroll
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(256) k_taps_scalar(TapArgs A, const V* __restr
     if (eb + lane < e1) {
       const int kk = A.key[eb + lane];
       const int lo = kk & 0xffff, off = kk >> 16;
-      c = ADJ ? (b + off - (mz - 1)) * A.n_ell + lo : lo * mz + a + off - (mz - 1);
+      c = ADJ ? (b + off - (mz - 1)) * A.n_ell + lo : lo * mz + a + off - (nz - 1);
       v = tap_w<V>(val[eb + lane]);
     }
     const int cnt = min(32, e1 - eb);
@@ -240,10 +245,10 @@ void srt_taps_free(SrtTaps* t) {
   *t = SrtTaps();
 }
 
-// T: rows m < n_ell, columns l*(2mz-1) + q (q = d + mz - 1), ascending.
+// T: rows m < n_ell, columns l*D + q (D = mz + n_zs - 1), ascending.
 int srt_build_taps(srt_plan_s* plan, const SrtCsr& T, int64_t* nnz2, int64_t* bytes) {
   const srt_geometry& g = plan->g;
-  const int mz = g.mz, n_ell = g.n_ell, D = 2 * mz - 1;
+  const int mz = g.mz, nz = g.n_zs, n_ell = g.n_ell, D = mz + nz - 1;
   if (T.rows != n_ell || n_ell > 0xffff || D > 0x7fff) return SRT_ERR_ARG;
   const int64_t nt = T.nnz;
   std::vector<int32_t> rp(n_ell + 1), col(nt);
@@ -255,9 +260,14 @@ int srt_build_taps(srt_plan_s* plan, const SrtCsr& T, int64_t* nnz2, int64_t* by
     if (T.v32) SRT_CUDA_TRY(cudaMemcpy(v32.data(), T.v32, nt * 4, cudaMemcpyDeviceToHost));
     if (T.v16) SRT_CUDA_TRY(cudaMemcpy(v16.data(), T.v16, nt * 2, cudaMemcpyDeviceToHost));
   }
-  // entries of A2: each tap at offset d serves the mz - |d| rings h with 0 <= h + d < mz
+  // entries of A2: the tap in column q serves the rings h < nz whose slab
+  // k = h + u, u = q - (nz - 1), lies in the volume
   int64_t n2 = 0;
-  for (int64_t e = 0; e < nt; ++e) n2 += mz - std::abs(col[e] % D - (mz - 1));
+  for (int64_t e = 0; e < nt; ++e) {
+    const int u = col[e] % D - (nz - 1);
+    const int h0 = std::max(0, -u), h1 = std::min(nz - 1, mz - 1 - u);
+    n2 += h1 >= h0 ? h1 - h0 + 1 : 0;
+  }
   *nnz2 = n2;
   // counting sorts, stable in T's (m, l, q) order
   const int64_t nsub = (int64_t)n_ell * D;
@@ -298,7 +308,7 @@ int srt_taps_apply(const srt_plan_s* plan, bool adjoint, int64_t r0, int64_t row
   if (!t.rowptr || rows <= 0 || ncols <= 0) return SRT_ERR_ARG;
   if (G > 0 && (int64_t)G * R != rows) G = 0;
   if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 1;
-  TapArgs A{t.rowptr, t.key, g.mz, g.n_ell, (int)r0, (int)rows, G, R, TG};
+  TapArgs A{t.rowptr, t.key, g.mz, g.n_zs, g.n_ell, (int)r0, (int)rows, G, R, TG};
   if (g.weight_dtype == SRT_BF16) {
     if (!t.w16) return SRT_ERR_ARG;
     return adjoint ? launch<uint16_t, true>(A, t.w16, x, ldx, y, ldy, ncols, st)

@@ -256,6 +256,8 @@ def test_workspace_and_argument_errors(srt, orc):
 
 
 TOEP = [dict(I.sizes("srt32")), dict(I.sizes("srt16fd")),
+        dict(ms=9, mz=7, dxy=0.4, dz=0.3, radius=5.0, n_phi=5, n_zs=11, n_ell=23, phi0=0.4,
+             zs=(-1.65 - 0.57, -2.22 + 3.3)),              # 11 rings spaced dz, offset
         dict(ms=9, mz=7, dxy=0.4, dz=0.3, radius=5.0, n_phi=5, n_zs=7, n_ell=23, phi0=0.4),
         dict(ms=12, mz=40, dxy=0.5, dz=0.2, radius=9.0, n_phi=6, n_zs=40, n_ell=19)]
 
@@ -297,20 +299,47 @@ def test_toeplitz_second_stage(srt, orc, sz, wdt):
     assert abs(lhs - rhs) / nrm <= ADJ_TOL
 
 
-def test_rings_off_the_slab_centres_use_csr(srt, orc):
-    """As many rings as slabs but shifted by 0.3 slab: the master tensor of
-    the taps is assembled for rings at the slab centres, so the plan must
-    store A2 as CSR here, and still match the oracle."""
-    sz = dict(ms=10, mz=8, dxy=0.5, dz=0.5, radius=6.0, n_phi=8, n_zs=8, n_ell=21,
-              zs=(-2.0 + 0.15, 2.0 + 0.15))
+SPACED = [  # rings spaced like the slabs (spacing dz = 0.5), off the slab centres
+    dict(ms=10, mz=8, dxy=0.5, dz=0.5, radius=6.0, n_phi=8, n_zs=8, n_ell=21,
+         zs=(-2.0 + 0.15, 2.0 + 0.15)),                     # shifted by 0.3 slab
+    dict(ms=10, mz=8, dxy=0.5, dz=0.5, radius=6.0, n_phi=8, n_zs=13, n_ell=21,
+         zs=(-3.2, 3.3)),                                   # more rings, past both ends
+    dict(ms=10, mz=8, dxy=0.5, dz=0.5, radius=6.0, n_phi=8, n_zs=3, n_ell=21,
+         zs=(-0.725, 0.775)),                               # fewer rings, off centre
+]
+
+
+@pytest.mark.parametrize("sz", SPACED)
+def test_rings_spaced_like_slabs_use_taps(srt, orc, sz):
+    """Rings spaced like the slabs, whatever their number and offset, make A2
+    Toeplitz in the slab offset: the plan applies it from the taps of a
+    master tensor assembled for a ring at that offset, and matches the
+    oracle and the CSR plan."""
     g, o = geom_pair(orc, **sz)
     plan = srt.Plan(g)
-    assert plan.info["a2_taps"] == 0 and plan.info["n_taps"] == 0
+    csr = srt.Plan(g.with_(csr_only=True))
+    assert plan.info["a2_taps"] == 1 and plan.info["n_taps"] > 0
+    assert plan.info["nnz2"] == csr.info["nnz2"]
     rng = np.random.default_rng(31)
     f = rng.uniform(0, 1, g.f_shape)
     y = rng.standard_normal(g.p_shape)
     assert rel_l2(to_np(plan.forward(to_dev(f))), orc.forward(o, f)) <= FP32_TOL
     assert rel_l2(to_np(plan.adjoint(to_dev(y))), orc.adjoint(o, y)) <= FP32_TOL
+    for which in (2, 4):
+        ra, ca, va, _ = plan.export(which)
+        rb, cb, vb, _ = csr.export(which)
+        np.testing.assert_array_equal(ra, rb)
+        np.testing.assert_array_equal(ca, cb)
+        assert rel_l2(va, vb) <= 1e-6
+
+
+def test_rings_spaced_unlike_slabs_use_csr(srt, orc):
+    g, o = geom_pair(orc, ms=10, mz=8, dxy=0.5, dz=0.5, radius=6.0, n_phi=8, n_zs=8, n_ell=21,
+                     zs=(-2.0, 2.2))                        # spacing 0.525
+    plan = srt.Plan(g)
+    assert plan.info["a2_taps"] == 0 and plan.info["n_taps"] == 0
+    f = np.random.default_rng(32).uniform(0, 1, g.f_shape)
+    assert rel_l2(to_np(plan.forward(to_dev(f))), orc.forward(o, f)) <= FP32_TOL
 
 
 def test_plan_info_and_timing(srt, orc):
