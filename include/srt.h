@@ -63,10 +63,12 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  * nodes); A2's entry (l, k) becomes node l's hat integrated along the
  * semicircle inside slab k, so A2 holds about twice the entries. */
 #define SRT_RHO_LINEAR 0x10
-/* When the rings sit at the slab centres (n_zs = mz over the volume height),
- * A2[(h,m),(l,k)] = T[m, k-h, l] for a master tensor T, and the plan applies A2
- * and A2^T from T's taps without storing them (srt_plan_info_t.a2_taps = 1),
- * unless SRT_CSR_ONLY is set. */
+/* When the rings are spaced like the slabs ((zs_hi - zs_lo) / n_zs = dz, any
+ * n_zs, any offset; e.g. n_zs = mz over the volume height), ring h sits at
+ * slab h + s plus a fixed fraction of a slab, A2[(h,m),(l,k)] = T[m, k-h-s, l]
+ * for a master tensor T, and the plan applies A2 and A2^T from T's taps
+ * without storing them (srt_plan_info_t.a2_taps = 1), unless SRT_CSR_ONLY is
+ * set (or mz + n_zs - 1 > 32767). */
 
 /*
  * Geometry (Sec. 3.1, Algorithm 1 inputs).  Lengths in mm, angles in rad.

@@ -35,11 +35,13 @@ struct SrtCsr {
   double* v64 = nullptr;      // nnz (SRT_KEEP_F64)
 };
 
-// Toeplitz form of A2 (toeplitz.cu), used when the rings sit at the slab
-// centres: A2[(h,m),(l,k)] = T[m, k - h, l].  Taps grouped in sub-rows so that
-// every output row of A2 (forward) or A2^T (adjoint) is one contiguous range:
-// forward sub-rows (m, d + mz - 1) listing l, key l | (d + mz - 1) << 16;
-// adjoint sub-rows (l, mz - 1 - d) listing m, key m | (mz - 1 - d) << 16.
+// Toeplitz form of A2 (toeplitz.cu), used when the rings are spaced like the
+// slabs (ring h at slab h + s plus a fixed fraction): A2[(h,m),(l,k)] =
+// T[m, k - h - s, l] over D = mz + n_zs - 1 offsets, column q of T at
+// offset q - (n_zs - 1) - s.  Taps grouped in sub-rows so that every output
+// row of A2 (forward) or A2^T (adjoint) is one contiguous range: forward
+// sub-rows (m, q) listing l, key l | q << 16; adjoint sub-rows
+// (l, D - 1 - q) listing m, key m | (D - 1 - q) << 16.
 struct SrtTaps {
   int64_t nsub = 0, nent = 0;
   int32_t* rowptr = nullptr;  // nsub + 1
