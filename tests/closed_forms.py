@@ -51,6 +51,29 @@ def arc_circle_rect(cx, cy, r, x0, x1, y0, y1) -> float:
     return r * t
 
 
+def arc_circle_rect_v(cx, cy, r, x0, x1, y0, y1) -> np.ndarray:
+    """arc_circle_rect over numpy arrays (broadcast).  The clamps of the
+    scalar version come from sqrt(max((r - u)(r + u), 0)) being 0 beyond the
+    circle: atan2 then gives 0 / pi resp. +-pi/2 there."""
+    def acos_r(u):
+        return np.arctan2(np.sqrt(np.maximum((r - u) * (r + u), 0.0)), u)
+
+    def asin_r(u):
+        return np.arctan2(u, np.sqrt(np.maximum((r - u) * (r + u), 0.0)))
+
+    def ov(lo, hi):
+        return np.maximum(0.0, hi - lo)
+
+    a1, a0 = acos_r(np.asarray(x1) - cx), acos_r(np.asarray(x0) - cx)
+    s0, s1 = asin_r(np.asarray(y0) - cy), asin_r(np.asarray(y1) - cy)
+    hp = 0.5 * PI
+    t = ov(np.maximum(0.0, np.maximum(a1, s0)), np.minimum(hp, np.minimum(a0, s1)))
+    t = t + ov(np.maximum(hp, np.maximum(a1, PI - s1)), np.minimum(PI, np.minimum(a0, PI - s0)))
+    t = t + ov(np.maximum(-PI, np.maximum(-a0, -PI - s1)), np.minimum(-hp, np.minimum(-a1, -PI - s0)))
+    t = t + ov(np.maximum(-hp, np.maximum(-a0, s0)), np.minimum(0.0, np.minimum(-a1, s1)))
+    return r * t
+
+
 def _ov_iv(*iv):
     lo = max(a for a, _ in iv)
     hi = min(b for _, b in iv)
