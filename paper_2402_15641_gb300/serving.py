@@ -279,6 +279,8 @@ class Server:
                 old = self.cost.get(ck)
                 self.cost[ck] = per if old is None else 0.8 * old + 0.2 * per
                 for i, r in enumerate(f.reqs):
+                    if r.error is not None:  # already failed at the deadline
+                        continue
                     if r.cancelled:
                         self.stats.cancelled += 1
                         continue
@@ -291,8 +293,12 @@ class Server:
                 f.ex.last_used = now
                 self.free_slots.append(f.slot)
             elif now > f.deadline:
-                for r in f.reqs:  # the host stops waiting; buffers stay busy
-                    self._fail(r, "timeout")
+                # the host stops waiting on these requests; the buffers stay
+                # busy until the batch completes, and its late results are
+                # dropped (each request is answered once)
+                for r in f.reqs:
+                    if not r.cancelled:
+                        self._fail(r, "timeout")
                 f.deadline = math.inf
                 still.append(f)
             else:
