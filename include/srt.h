@@ -61,7 +61,7 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  * constant from ell_lo to rho_0 and from rho_{n_ell-1} to ell_hi, zero
  * outside [ell_lo, ell_hi].  A1 is unchanged (it samples f^{1,2} at the
  * nodes); A2's entry (l, k) becomes node l's hat integrated along the
- * semicircle inside slab k, so A2 holds about twice the entries. */
+ * semicircle inside slab k, so A2 holds more entries (1.49x at 256^3). */
 #define SRT_RHO_LINEAR 0x10
 /* When the rings are spaced like the slabs ((zs_hi - zs_lo) / n_zs = dz, any
  * n_zs, any offset; e.g. n_zs = mz over the volume height), ring h sits at
