@@ -26,7 +26,6 @@ payloads, schedules and keeps time.
 from __future__ import annotations
 
 import collections
-import heapq
 import math
 import time
 from dataclasses import dataclass, field

@@ -10,7 +10,6 @@ Layouts (float32, contiguous, on the plan's device):
 from __future__ import annotations
 
 import ctypes
-import math
 from dataclasses import dataclass, asdict, replace
 
 import numpy as np

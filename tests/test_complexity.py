@@ -9,7 +9,6 @@ view), the oracle's own weights give
   * voxels per shell proportional to s^2, so the direct sum over s^3 shells
     costs s^5 = M^{5/3}.
 Slopes are fitted over s = 8, 16, 32 on seeded samples of rows and shells."""
-import math
 
 import numpy as np
 

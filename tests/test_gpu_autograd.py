@@ -1,7 +1,6 @@
 """Differentiation through the SRT (autograd backward = adjoint kernel):
 central finite differences, the oracle's FP64 adjoint, and the least-squares
 reconstruction on the 128^3 workload."""
-import math
 
 import numpy as np
 import pytest

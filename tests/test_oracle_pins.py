@@ -17,7 +17,7 @@ import math
 import numpy as np
 import pytest
 
-from tests.closed_forms import arc_circle_rect, geometry_numbers
+from tests.closed_forms import arc_circle_rect
 
 
 def _tiny(O, **kw):
