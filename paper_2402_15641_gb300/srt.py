@@ -92,6 +92,9 @@ def _ptr(t: torch.Tensor) -> int:
     return t.data_ptr()
 
 
+_CPU = torch.device("cpu")
+
+
 class Plan:
     """An assembled operator pair (A1, A2 and transposes) resident on one GPU."""
 
@@ -144,15 +147,41 @@ class Plan:
             return t.shape[0]
         raise ValueError(f"shape {tuple(t.shape)} does not match {tuple(shape)}")
 
+    # The library takes raw pointers: a tensor on the wrong device or an output
+    # that is too small would be read or written out of bounds, so both are
+    # refused here, before any call.
+    @staticmethod
+    def _on(t: torch.Tensor, device: torch.device, what: str) -> None:
+        if t.device != device:
+            raise ValueError(f"{what} must be on {device}, not {t.device}")
+
+    def _out(self, t: torch.Tensor, batch: int, shape, device: torch.device, what: str) -> None:
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous float32 tensor")
+        self._on(t, device, what)
+        if t.numel() != batch * int(np.prod(shape)):
+            raise ValueError(f"{what}: shape {tuple(t.shape)} does not hold {batch} x "
+                             f"{tuple(shape)}")
+
+    def _workspace(self, ws: torch.Tensor) -> tuple[int, int]:
+        """(pointer, size in bytes) of a caller's device workspace."""
+        self._on(ws, self.device, "workspace")
+        if not ws.is_contiguous():
+            raise ValueError("workspace must be contiguous")
+        return _ptr(ws), ws.numel() * ws.element_size()
+
     def forward(self, f: torch.Tensor, out: torch.Tensor | None = None, workspace=None,
                 stream=None) -> torch.Tensor:
         """p = A f (Algorithm 1 on every sensor column)."""
         B = self._batch(f, self.geom.f_shape)
+        self._on(f, self.device, "f")
         if out is None:
             shape = self.geom.p_shape if f.dim() == 3 else (B, *self.geom.p_shape)
             out = torch.empty(shape, dtype=torch.float32, device=f.device)
-        ws = self.workspace(B) if workspace is None else workspace
-        check(self._lib.srt_forward(self._h, _ptr(f), _ptr(out), B, _ptr(ws), ws.numel(),
+        else:
+            self._out(out, B, self.geom.p_shape, self.device, "out")
+        ws, nb = self._workspace(self.workspace(B) if workspace is None else workspace)
+        check(self._lib.srt_forward(self._h, _ptr(f), _ptr(out), B, ws, nb,
                                     ctypes.c_void_p(_stream_ptr(stream))), "srt_forward")
         return out
 
@@ -160,28 +189,36 @@ class Plan:
                 stream=None) -> torch.Tensor:
         """f' = A^T p (Algorithm 2, matched adjoint)."""
         B = self._batch(p, self.geom.p_shape)
+        self._on(p, self.device, "p")
         if out is None:
             shape = self.geom.f_shape if p.dim() == 3 else (B, *self.geom.f_shape)
             out = torch.empty(shape, dtype=torch.float32, device=p.device)
-        ws = self.workspace(B) if workspace is None else workspace
-        check(self._lib.srt_adjoint(self._h, _ptr(p), _ptr(out), B, _ptr(ws), ws.numel(),
+        else:
+            self._out(out, B, self.geom.f_shape, self.device, "out")
+        ws, nb = self._workspace(self.workspace(B) if workspace is None else workspace)
+        check(self._lib.srt_adjoint(self._h, _ptr(p), _ptr(out), B, ws, nb,
                                     ctypes.c_void_p(_stream_ptr(stream))), "srt_adjoint")
         return out
 
     def forward_host(self, f_host: torch.Tensor, out_host: torch.Tensor, stream=None):
         """End-to-end forward on host tensors (copies inside the call)."""
         B = self._batch(f_host, self.geom.f_shape)
-        ws = self.workspace(B, host=True)
-        check(self._lib.srt_forward_host(self._h, _ptr(f_host), _ptr(out_host), B, _ptr(ws),
-                                         ws.numel(), ctypes.c_void_p(_stream_ptr(stream))),
+        self._on(f_host, _CPU, "f_host")
+        self._out(out_host, B, self.geom.p_shape, _CPU, "out_host")
+        ws, nb = self._workspace(self.workspace(B, host=True))
+        check(self._lib.srt_forward_host(self._h, _ptr(f_host), _ptr(out_host), B, ws, nb,
+                                         ctypes.c_void_p(_stream_ptr(stream))),
               "srt_forward_host")
         return out_host
 
     def adjoint_host(self, p_host: torch.Tensor, out_host: torch.Tensor, stream=None):
+        """End-to-end adjoint on host tensors (copies inside the call)."""
         B = self._batch(p_host, self.geom.p_shape)
-        ws = self.workspace(B, host=True)
-        check(self._lib.srt_adjoint_host(self._h, _ptr(p_host), _ptr(out_host), B, _ptr(ws),
-                                         ws.numel(), ctypes.c_void_p(_stream_ptr(stream))),
+        self._on(p_host, _CPU, "p_host")
+        self._out(out_host, B, self.geom.f_shape, _CPU, "out_host")
+        ws, nb = self._workspace(self.workspace(B, host=True))
+        check(self._lib.srt_adjoint_host(self._h, _ptr(p_host), _ptr(out_host), B, ws, nb,
+                                         ctypes.c_void_p(_stream_ptr(stream))),
               "srt_adjoint_host")
         return out_host
 
@@ -290,6 +327,9 @@ def dot_f64(a: torch.Tensor, b: torch.Tensor, stream=None) -> float:
     """FP64 inner product of two float32 device tensors (deterministic)."""
     if a.numel() != b.numel() or a.dtype != torch.float32 or b.dtype != torch.float32:
         raise ValueError("dot_f64 needs two float32 tensors of equal size")
+    if a.device.type != "cuda" or b.device != a.device:
+        raise ValueError(f"dot_f64 needs both tensors on one CUDA device, not {a.device}, "
+                         f"{b.device}")
     a, b = a.contiguous(), b.contiguous()
     lib = L.lib()
     dev = a.device
