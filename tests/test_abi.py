@@ -150,3 +150,15 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.lib()
 
+
+
+@pytest.mark.parametrize("compiler,std,ext", [("gcc", "-std=c99", "c"), ("g++", "-std=c++11", "cpp")])
+def test_header_is_strict_c99_and_cxx11(tmp_path, compiler, std, ext):
+    """The boundary header compiles warning-free as C99 and as C++11 (its
+    extern "C" block), with -Wall -Wextra -pedantic -Werror."""
+    src = tmp_path / f"probe.{ext}"
+    src.write_text('#include "srt.h"\n'
+                   "int main(void) { srt_geometry g; srt_plan_info_t i; (void)g; (void)i;\n"
+                   "  return SRT_OK; }\n")
+    subprocess.run([compiler, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), "-fsyntax-only", str(src)], check=True)
