@@ -9,9 +9,15 @@ paper's discretisation, Sec. 2 and Sec. 3.1 / Algorithm 1 of the paper, without
 forming the two CRT matrices).  This file builds it with gcc and marshals
 numpy arrays.
 
-Parity status: every exported function is pinned by ``tests/test_oracle_*.py``
-(closed-form ball, brute-force shell sampling, analytic arc lengths, adjoint
-identity, symmetries, a hand-computed one-voxel case).
+Parity status: every exported function is pinned by ``tests/test_oracle_*.py``:
+- the closed-form ball;
+- brute-force shell sampling, with the in-plane radius snapped, interpolated
+  and exact (the continuum limit);
+- analytic arc lengths and first moments;
+- coarea area sums;
+- the adjoint identity;
+- symmetries;
+- a hand-computed one-voxel case.
 """
 from __future__ import annotations
 
