@@ -44,7 +44,7 @@ def parse():
     p.add_argument("--csr-only", action="store_true",
                    help="store A2, A2^T as CSR instead of applying them from the Toeplitz taps")
     p.add_argument("--a1-rotation", action="store_true",
-                   help="store A1 for a quarter of the sensor columns (4x smaller, slower)")
+                   help="store A1 for a quarter of the sensor columns (4x less A1 memory, same speed)")
     p.add_argument("--rho-linear", action="store_true",
                    help="piecewise-linear intermediate in rho (else constant on the radius bins)")
     p.add_argument("--no-cpu-baseline", action="store_true")
