@@ -69,6 +69,23 @@ def test_oracle_arc_in_box_matches_closed_form(orc):
         assert abs(a - b) <= 1e-12 * max(1.0, r), (cx, cy, r, x0, x1, y0, y1, a, b)
 
 
+
+def test_oracle_arc_in_box_at_degenerate_positions(orc):
+    """Circles tangent to an edge from inside or outside, through a corner,
+    centred on an edge or a corner: the cases random boxes never hit
+    (boundary ties have measure zero, so the length is still exact)."""
+    x0, x1, y0, y1 = -1.0, 1.0, -0.5, 0.5
+    n = 0
+    for cx, cy in [(0.0, 0.0), (0.3, -0.2), (1.0, 1.0), (0.5, 0.0), (1.0, 0.5)]:
+        radii = [x1 - cx, cx - x0, y1 - cy, cy - y0, math.hypot(x1 - cx, y1 - cy),
+                 math.hypot(x0 - cx, y0 - cy), abs(x1 - cx) + 1.0, 0.25]
+        for r in [r for r in radii if r > 0]:
+            a = orc.arc_in_box(cx, cy, r, x0, x1, y0, y1)
+            b = arc_circle_rect(cx, cy, r, x0, x1, y0, y1)
+            assert abs(a - b) <= 1e-12 * max(1.0, r), (cx, cy, r, a, b)
+            n += 1
+    assert n >= 30
+
 # ----------------------------------------------------- per-entry arc lengths
 def test_circle_arcs_match_closed_form(orc):
     g = _tiny(orc)
