@@ -82,6 +82,13 @@ def _arc_cases(rng, n):
               (0.3, -0.2, 1.5, -5.0, 5.0, -5.0, 5.0), (0.0, 0.0, 1.0, 2.0, 3.0, -1.0, 1.0),
               (0.0, 0.0, 2.0, 1.0, 5.0, -5.0, 5.0), (0.0, 5.0, 1.0, -1.0, 1.0, 4.0, 6.0),
               (0.0, 5.0, 1.0, -0.5, 0.5, 5.5, 6.0)]
+    # tangent to each edge from inside and outside, through corners
+    x0, x1, y0, y1 = -1.0, 1.0, -0.5, 0.5
+    for cx, cy in [(0.0, 0.0), (0.3, -0.2), (1.0, 1.0), (0.5, 0.0), (1.0, 0.5)]:
+        for r in [x1 - cx, cx - x0, y1 - cy, cy - y0, math.hypot(x1 - cx, y1 - cy),
+                  math.hypot(x0 - cx, y0 - cy), abs(x1 - cx) + 1.0]:
+            if r > 0:
+                cases.append((cx, cy, r, x0, x1, y0, y1))
     return cases
 
 
