@@ -132,7 +132,9 @@ static void ws_free(orc_ws* w) {
 /* ------------------------------------------------- in-plane circle walk
  * Circle centre (sx, sy), radius rho, in the (x, y) plane of the pixel grid.
  * Breakpoints: every angle where the circle meets a grid line x = const or
- * y = const.  Each arc between consecutive breakpoints lies in one pixel
+ * y = const, including a line it only touches (|u| = rho): the point of
+ * contact splits the arc around it, so that no arc's midpoint lies on a grid
+ * line.  Each arc between consecutive breakpoints then lies in one pixel
  * (the one holding its midpoint).  Output: (pixel ix*ms+iy, arc length)
  * for arcs inside the grid.  Returns the number of arcs written.          */
 static int circle_walk(const orc_geom* g, double sx, double sy, double rho, double* ab,
@@ -141,7 +143,7 @@ static int circle_walk(const orc_geom* g, double sx, double sy, double rho, doub
   int n = 0;
   for (int i = 0; i <= g->ms; ++i) {
     double u = -hx + i * g->dxy - sx; /* x-line offset from centre */
-    if (fabs(u) < rho) {
+    if (fabs(u) <= rho) {
       double v = sqrt((rho - u) * (rho + u));
       ab[n++] = wrap_2pi(atan2(v, u));
       ab[n++] = wrap_2pi(atan2(-v, u));
@@ -149,7 +151,7 @@ static int circle_walk(const orc_geom* g, double sx, double sy, double rho, doub
   }
   for (int i = 0; i <= g->ms; ++i) {
     double u = -hx + i * g->dxy - sy; /* y-line offset from centre */
-    if (fabs(u) < rho) {
+    if (fabs(u) <= rho) {
       double v = sqrt((rho - u) * (rho + u));
       ab[n++] = wrap_2pi(atan2(u, v));
       ab[n++] = wrap_2pi(atan2(u, -v));

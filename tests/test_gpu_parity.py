@@ -157,6 +157,36 @@ def test_ragged_geometries_full(srt, orc, sz, batch):
     assert rel_l2(to_np(plan.adjoint(to_dev(y))), fa) <= FP32_TOL
 
 
+@pytest.mark.parametrize("mode", [{}, dict(a1_rotation=True), dict(csr_only=True),
+                                  dict(rho_linear=True)])
+def test_tangent_geometry_entries_and_transforms(srt, orc, mode):
+    """Circles that touch a pixel line from either side, or the box from
+    outside (the tangent geometry of the oracle pins): every A1 and A2 entry
+    against the oracle's arcs, and forward / adjoint against the oracle."""
+    from tests.test_oracle_pins import TANGENT
+    g, o = geom_pair(orc, keep_f64=True, **TANGENT, **mode)
+    plan = srt.Plan(g)
+    rp, col, _, v64 = plan.export(1, f64=True)
+    for r in range(g.n_phi * g.n_ell):
+        j, l = divmod(r, g.n_ell)
+        _arcs_match(col[rp[r]:rp[r + 1]], v64[rp[r]:rp[r + 1]], orc.circle_arcs(o, j, l), g.dxy)
+    # radius 1.5 touches the box from outside: no entry at all
+    for j in range(g.n_phi):
+        assert rp[j * g.n_ell + 1] == rp[j * g.n_ell]
+    rp, col, _, v64 = plan.export(2, f64=True)
+    for r in range(g.n_zs * g.n_ell):
+        h, m = divmod(r, g.n_ell)
+        _arcs_match(col[rp[r]:rp[r + 1]], v64[rp[r]:rp[r + 1]], orc.semicircle_arcs(o, h, m),
+                    g.dz)
+    rng = np.random.default_rng(17)
+    f = rng.uniform(0, 1, (2, *g.f_shape))
+    y = rng.standard_normal((2, *g.p_shape))
+    pf = np.stack([orc.forward(o, f[b]) for b in range(2)])
+    fa = np.stack([orc.adjoint(o, y[b]) for b in range(2)])
+    assert rel_l2(to_np(plan.forward(to_dev(f))), pf) <= FP32_TOL
+    assert rel_l2(to_np(plan.adjoint(to_dev(y))), fa) <= FP32_TOL
+
+
 def test_fd16_full_and_batched_bitwise(srt, orc):
     import torch
     sz = dict(I.sizes("srt16fd"))

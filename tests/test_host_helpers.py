@@ -104,3 +104,17 @@ def test_arc_length_and_moment(run):
         assert abs(length - want) <= 1e-12 * max(1.0, r), (c, length, want)
         assert abs(length_m - length) <= 1e-13 * max(1.0, r), (c, length_m, length)
         assert abs(my - want_m) <= 1e-12 * max(1.0, r * (r + abs(cy))), (c, my, want_m)
+
+
+def test_arc_length_against_oracle_walk_at_degenerate_positions(run, orc):
+    """The tangent, corner and edge-centred cases once more, now against the
+    oracle's arc_in_box: sorted breakpoints and an open-box midpoint test, a
+    method unlike the quarter intervals that both the library helper and
+    the closed form use, so an error shared by those two still shows here."""
+    cases = _arc_cases(np.random.default_rng(13), 0)
+    got = run([" ".join(["arc"] + [float(v).hex() for v in c]) for c in cases])
+    vals = np.array([float.fromhex(g) for g in got]).reshape(-1, 3)
+    assert len(cases) >= 35
+    for c, (length, _, _) in zip(cases, vals):
+        want = orc.arc_in_box(*c)
+        assert abs(length - want) <= 1e-12 * max(1.0, c[2]), (c, length, want)

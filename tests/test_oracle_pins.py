@@ -87,6 +87,95 @@ def test_oracle_arc_in_box_at_degenerate_positions(orc):
     assert n >= 30
 
 # ----------------------------------------------------- per-entry arc lengths
+# A 3 x 3 grid of unit pixels (lines at -1.5, -0.5, 0.5, 1.5) seen from four
+# sensors at distance 3 on the axes, with radius-bin centres 1.5, 2.5, 3.5 and
+# 4.5: every circle of columns 0 and 2 touches an x-line at its nearest or
+# farthest point, every circle of columns 1 and 3 a y-line.  From the low
+# side (column 2: the rightmost point on a line; column 3: the topmost) and
+# from the high side (columns 0, 1); radius 1.5 touches the box boundary from
+# outside (no arc lies in the box), radius 4.5 touches it from inside.
+TANGENT = dict(ms=3, mz=2, dxy=1.0, dz=1.0, radius=3.0, n_phi=4, phi0=0.0, n_zs=1, zs=(-1.0, 1.0),
+               n_ell=4, ell=(1.0, 5.0))
+
+
+def tangent_geometry(O, rho_linear=False):
+    t = TANGENT
+    return O.OracleGeometry(t["ms"], t["mz"], t["dxy"], t["dz"], t["radius"], t["n_phi"],
+                            t["phi0"], t["n_zs"], t["zs"][0], t["zs"][1], t["n_ell"],
+                            t["ell"][0], t["ell"][1], rho_linear)
+
+
+def _sampled_arcs(sx, sy, rho, ms, dxy, n=400_000):
+    """Arc per pixel by dense midpoint sampling of the angle: each sample
+    carries rho * 2 pi / n and goes to the pixel it falls in.  Independent of
+    both breakpoint walks and closed forms; exact to O(rho / n) per crossing."""
+    a = (np.arange(n) + 0.5) * (2 * math.pi / n)
+    hx = 0.5 * ms * dxy
+    ix = np.floor((sx + rho * np.cos(a) + hx) / dxy).astype(np.int64)
+    iy = np.floor((sy + rho * np.sin(a) + hx) / dxy).astype(np.int64)
+    ok = (ix >= 0) & (ix < ms) & (iy >= 0) & (iy < ms)
+    return np.bincount(ix[ok] * ms + iy[ok], minlength=ms * ms) * (rho * 2 * math.pi / n)
+
+
+def test_circle_walk_at_tangent_positions(orc):
+    """A circle that touches a pixel line must not move the arc around the
+    point of contact into the pixel across that line (the arc's midpoint lies
+    on the line); one that touches the box from outside has no arc inside."""
+    g = tangent_geometry(orc)
+    G = _grid(g)
+    touched = 0
+    for j in range(g.n_phi):
+        sx, sy = g.radius * math.cos(G["phi"][j]), g.radius * math.sin(G["phi"][j])
+        for l in range(g.n_ell):
+            rho = G["ell"][l]
+            near = abs(sx) - rho if j % 2 == 0 else abs(sy) - rho
+            assert any(abs(abs(near) - abs(b)) < 1e-15 for b in G["xb"])  # really tangent
+            touched += 1
+            got = orc.circle_arcs(g, j, l)
+            samp = _sampled_arcs(sx, sy, rho, g.ms, g.dxy)
+            for ix in range(g.ms):
+                for iy in range(g.ms):
+                    want = arc_circle_rect(sx, sy, rho, G["xb"][ix], G["xb"][ix + 1],
+                                           G["xb"][iy], G["xb"][iy + 1])
+                    have = got.get(ix * g.ms + iy, 0.0)
+                    assert abs(have - want) <= 1e-12 * rho, (j, l, ix, iy, have, want)
+                    assert abs(have - samp[ix * g.ms + iy]) <= 1e-4, (j, l, ix, iy, have)
+            if l == 0:  # radius 1.5 touches the box from outside
+                assert got == {}, (j, got)
+    assert touched == 16
+    # the case that first showed the fault: sensor (-3, 0), radius 2.5, its
+    # rightmost point on x = -0.5; the arc around it belongs to pixel (0, 1)
+    got = orc.circle_arcs(g, 2, 1)
+    want = arc_circle_rect(-3.0, 0.0, 2.5, -1.5, -0.5, -0.5, 0.5)
+    assert want > 1.0 and abs(got.get(0 * 3 + 1, 0.0) - want) <= 1e-12
+    assert 1 * 3 + 1 not in got
+
+
+def test_forward_at_tangent_positions_matches_closed_forms(orc):
+    """The whole shell walk at the tangent geometry, for the separable
+    volume f = q[ix, iy] s[k]: p[j,h,m] = sum_{k,l} s[k] arc2(h,m;k,l)
+    sum_pix q[pix] arc1(j,l;pix) with every arc from the closed form."""
+    g = tangent_geometry(orc)
+    G = _grid(g)
+    rng = np.random.default_rng(21)
+    q = rng.uniform(0.1, 1.0, (g.ms, g.ms))
+    s = rng.uniform(0.1, 1.0, g.mz)
+    f = q[:, :, None] * s[None, None, :]
+    p = orc.forward(g, f)
+    for j in range(g.n_phi):
+        sx, sy = g.radius * math.cos(G["phi"][j]), g.radius * math.sin(G["phi"][j])
+        inner = [sum(q[ix, iy] * arc_circle_rect(sx, sy, G["ell"][l], G["xb"][ix],
+                                                  G["xb"][ix + 1], G["xb"][iy], G["xb"][iy + 1])
+                     for ix in range(g.ms) for iy in range(g.ms)) for l in range(g.n_ell)]
+        for h in range(g.n_zs):
+            for m in range(g.n_ell):
+                want = sum(s[k] * arc_circle_rect(G["zh"][h], 0.0, G["ell"][m], G["zb"][k],
+                                                  G["zb"][k + 1], G["edges"][l],
+                                                  G["edges"][l + 1]) * inner[l]
+                           for k in range(g.mz) for l in range(g.n_ell))
+                assert abs(p[j, h, m] - want) <= 1e-12 * max(1.0, abs(want)), (j, h, m)
+
+
 def test_circle_arcs_match_closed_form(orc):
     g = _tiny(orc)
     G = _grid(g)
