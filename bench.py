@@ -28,7 +28,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SRT fwd+adj ops/s & HBM GB/s vs peak at 256^3"
 UNIT = "fwd+adj pairs/s"
-N_SM = 152
 FP32_LANES_PER_SM = 128
 
 
@@ -52,7 +51,9 @@ def parse():
     return p.parse_args()
 
 
-def peaks():
+def peaks(n_sm):
+    """Roofline denominators: measured HBM copy bandwidth and SM clock, and
+    the FP32 FMA peak derived from the device's SM count and that clock."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = {}
     if os.path.exists(path):
@@ -61,10 +62,10 @@ def peaks():
     hbm = d.get("hbm_gbs", 6800.0)
     sm_max = d.get("sm_max_mhz", 2070.0)
     src = "measured" if "hbm_gbs" in d else "fallback"
-    # FP32 FMA peak from unit counts and the maximum SM clock: 152 SMs x 128
+    # FP32 FMA peak from unit counts and the maximum SM clock: SMs x 128
     # FP32 lanes x 2 FLOP per FMA x clock.
-    fp32 = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    return dict(hbm_gbs=hbm, fp32_tflops=fp32, sm_max_mhz=sm_max, src=src)
+    fp32 = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    return dict(hbm_gbs=hbm, fp32_tflops=fp32, sm_max_mhz=sm_max, src=src, n_sm=n_sm)
 
 
 class Clocks:
@@ -335,7 +336,7 @@ def run_ours(args):
     from paper_2402_15641_gb300.srt import Geometry, Pipeline, Plan, fp32_fma_peak
 
     build.build()
-    pk = peaks()
+    pk = peaks(torch.cuda.get_device_properties(local).multi_processor_count)
     sz = I.sizes(args.workload)
     geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only,
                                a1_rotation=args.a1_rotation, rho_linear=args.rho_linear)
@@ -403,12 +404,12 @@ def run_ours(args):
             stages[f"{d}.{name}"] = s
     dom = max(stages, key=lambda k: stages[k]["ms"])
     ds = stages[dom]
-    delivery = 152 * 32 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    delivery = pk["n_sm"] * 32 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     if "tflop_s" in ds:
         roof = {"bound": "alu", "achieved": ds["tflop_s"], "peak": round(pk["fp32_tflops"], 2),
                 "unit": "TFLOP/s", "frac": ds["fp32_frac"],
                 "traffic": ncu_traffic(dom, args.workload), "kernel": dom,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock "
+                "peak_source": f"derived: {pk['n_sm']} SMs x 128 FP32 lanes x 2 x max SM clock "
                                f"{pk['sm_max_mhz']:.0f} MHz",
                 "fma_measured_tflops": round(fma_meas, 2),
                 "frac_of_measured_fma": round(ds["tflop_s"] / fma_meas, 4),

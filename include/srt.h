@@ -148,8 +148,10 @@ int srt_workspace_bytes(srt_plan_t plan, int32_t batch, size_t* bytes);
  *   p: device, float[batch][n_phi][n_zs][n_ell] (overwritten, never accumulated)
  *   workspace: device, >= srt_workspace_bytes(batch), 256-byte aligned; the
  *   caller owns it; concurrent calls need distinct workspaces.
- * f, p must be 16-byte aligned.  Asynchronous on `stream`.
- * Errors: SRT_ERR_ARG, SRT_ERR_WORKSPACE, SRT_ERR_CUDA (launch failure).
+ * f, p must be 16-byte aligned.  Asynchronous on `stream`.  The device that
+ * was current when the plan was made must be current.
+ * Errors: SRT_ERR_ARG (also: another device current), SRT_ERR_WORKSPACE,
+ * SRT_ERR_CUDA (launch failure).
  */
 int srt_forward(srt_plan_t plan, const float* f, float* p, int32_t batch, void* workspace,
                 size_t workspace_bytes, void* stream);
@@ -174,7 +176,10 @@ int srt_adjoint(srt_plan_t plan, const float* p, float* f, int32_t batch, void* 
  * bitwise those of srt_forward / srt_adjoint.  These calls record no
  * per-stage timing.  `workspace` must hold srt_host_workspace_bytes(batch)
  * bytes of device memory (device copies of input and output plus the
- * transform workspace).  Errors: as srt_forward.
+ * transform workspace).  The copy stream and its events come from a pool on
+ * the plan, created at a call's first use and reused by later calls (a call
+ * that overlaps another on the same plan takes a second set).
+ * Errors: as srt_forward.
  */
 int srt_host_workspace_bytes(srt_plan_t plan, int32_t batch, size_t* bytes);
 int srt_forward_host(srt_plan_t plan, const float* f_host, float* p_host, int32_t batch,
@@ -194,8 +199,8 @@ int srt_adjoint_host(srt_plan_t plan, const float* p_host, float* f_host, int32_
  *     plus one transform workspace) and three streams of its own (input
  *     copies, computation, result copies).  More slots give a slow copy
  *     more time to finish before its call's transform is due.  Errors:
- *     SRT_ERR_ARG (slots outside 2-4), SRT_ERR_OOM, SRT_ERR_CUDA; on error
- *     *pipe is set to NULL.
+ *     SRT_ERR_ARG (slots outside 2-4, or another device current than the
+ *     plan's), SRT_ERR_OOM, SRT_ERR_CUDA; on error *pipe is set to NULL.
  *   srt_pipe_submit: enqueue one call (direction 0 = forward, f_host ->
  *     p_host; 1 = adjoint, p_host -> f_host) and return without waiting;
  *     *ticket (may be NULL) numbers the calls 0, 1, 2, ...  Call i uses slot
@@ -203,8 +208,8 @@ int srt_adjoint_host(srt_plan_t plan, const float* p_host, float* f_host, int32_
  *     that slot's input.  in_host and out_host must stay allocated and unchanged
  *     (out_host unread) until srt_pipe_wait(ticket) has returned SRT_OK;
  *     pinned memory gives full copy speed.  The calls run in submission
- *     order.  Errors: SRT_ERR_ARG (null pipe or buffer, bad direction),
- *     SRT_ERR_CUDA.
+ *     order.  Errors: SRT_ERR_ARG (null pipe or buffer, bad direction,
+ *     another device current than the plan's), SRT_ERR_CUDA.
  *   srt_pipe_wait: block until call `ticket`'s result is in its host buffer
  *     (polling, at most timeout_s seconds; a negative timeout waits without
  *     limit).  Errors: SRT_ERR_ARG (unknown ticket), SRT_ERR_TIMEOUT,
@@ -241,7 +246,9 @@ int srt_pipe_destroy(srt_pipe_t pipe);
  *     plan was made on a different device than the current one.
  *   - The first call on a device looks up the scratch array's device address
  *     (a runtime call, cudaGetSymbolAddress); make that first call before any
- *     stream capture begins.
+ *     stream capture begins.  The address is kept for the life of the
+ *     process: calls after cudaDeviceReset on that device are not supported
+ *     (the reset unloads the library's device code and may move the array).
  *   - All calls on a device share the scratch, which keeps the last call's
  *     contents (no element needs to start at zero).  Calls whose work overlaps
  *     on the GPU race on it: order them on one stream.

@@ -12,6 +12,7 @@
 #include <math.h>
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <utility>
@@ -50,20 +51,7 @@ int check_geometry(const srt_geometry& g) {
   return SRT_OK;
 }
 
-void free_plan(srt_plan_s* p) {
-  if (!p) return;
-  srt_csr_free(&p->a1);
-  srt_csr_free(&p->a2);
-  srt_csr_free(&p->a1t);
-  srt_csr_free(&p->a2t);
-  srt_taps_free(&p->tf);
-  srt_taps_free(&p->ta);
-  srt_csr_free(&p->tm);
-  for (int d = 0; d < 2; ++d)
-    for (int i = 0; i < 5; ++i)
-      if (p->ev[d][i]) cudaEventDestroy(p->ev[d][i]);
-  delete p;
-}
+void free_plan(srt_plan_s* p);
 
 inline void mark(srt_plan_s* p, int dir, int i, cudaStream_t st) {
   if (p->timing) cudaEventRecord(p->ev[dir][i], st);
@@ -96,6 +84,75 @@ struct HostSink {
   cudaEvent_t ev[kHostChunks] = {};
   cudaEvent_t t0 = nullptr;  // when set, recorded on cs before the first copy
 };
+
+}  // namespace
+
+// Copy streams (with their chunk events) of host-buffer calls, kept on the
+// plan: a call takes an idle set, or creates one when every set is in use by
+// a concurrent call, and returns it when it has synchronised, so a sequence
+// of calls creates no stream or event after the first.
+struct SrtHostPool {
+  struct Set {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[kHostChunks] = {};
+  };
+  std::mutex mu;
+  std::vector<Set> idle;
+};
+
+namespace {
+
+void host_set_destroy(SrtHostPool::Set& s) {
+  for (cudaEvent_t& e : s.ev)
+    if (e) cudaEventDestroy(e);
+  if (s.cs) cudaStreamDestroy(s.cs);
+  s = SrtHostPool::Set();
+}
+
+int host_set_take(srt_plan_s* p, SrtHostPool::Set* out) {
+  {
+    std::lock_guard<std::mutex> lk(p->host_pool->mu);
+    if (!p->host_pool->idle.empty()) {
+      *out = p->host_pool->idle.back();
+      p->host_pool->idle.pop_back();
+      return SRT_OK;
+    }
+  }
+  SrtHostPool::Set s;
+  bool ok = cudaStreamCreateWithFlags(&s.cs, cudaStreamNonBlocking) == cudaSuccess;
+  for (cudaEvent_t& e : s.ev)
+    if (ok) ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    host_set_destroy(s);
+    return SRT_ERR_CUDA;
+  }
+  *out = s;
+  return SRT_OK;
+}
+
+void host_set_give(srt_plan_s* p, SrtHostPool::Set& s) {
+  std::lock_guard<std::mutex> lk(p->host_pool->mu);
+  p->host_pool->idle.push_back(s);
+}
+
+void free_plan(srt_plan_s* p) {
+  if (!p) return;
+  srt_csr_free(&p->a1);
+  srt_csr_free(&p->a2);
+  srt_csr_free(&p->a1t);
+  srt_csr_free(&p->a2t);
+  srt_taps_free(&p->tf);
+  srt_taps_free(&p->ta);
+  srt_csr_free(&p->tm);
+  for (int d = 0; d < 2; ++d)
+    for (int i = 0; i < 5; ++i)
+      if (p->ev[d][i]) cudaEventDestroy(p->ev[d][i]);
+  if (p->host_pool) {
+    for (SrtHostPool::Set& s : p->host_pool->idle) host_set_destroy(s);
+    delete p->host_pool;
+  }
+  delete p;
+}
 
 // How the A1 products reach the rows the plan did not store (SrtRot).
 SrtRot a1_rot(const srt_plan_s* p, int mode) {
@@ -222,10 +279,19 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   return SRT_OK;
 }
 
+// The plan's matrices live on the device it was built on: a call made with
+// another device current would launch there with pointers into the plan's
+// device memory, so it is refused before any work.
+int check_device(const srt_plan_s* plan) {
+  int dev = -1;
+  SRT_CUDA_TRY(cudaGetDevice(&dev));
+  return dev == plan->device ? SRT_OK : SRT_ERR_ARG;
+}
+
 int common_checks(srt_plan_t plan, const void* a, const void* b, int32_t batch) {
   if (!plan || !a || !b || batch <= 0) return SRT_ERR_ARG;
   if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) return SRT_ERR_ARG;
-  return SRT_OK;
+  return check_device(plan);
 }
 
 }  // namespace
@@ -261,9 +327,14 @@ int srt_plan(const srt_geometry* g, void* stream, srt_plan_t* out) {
   SRT_TRY(check_geometry(*g));
   srt_plan_s* p = new (std::nothrow) srt_plan_s();
   if (!p) return SRT_ERR_OOM;
+  p->host_pool = new (std::nothrow) SrtHostPool();
+  if (!p->host_pool) {
+    delete p;
+    return SRT_ERR_OOM;
+  }
   p->g = *g;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
-    delete p;
+    free_plan(p);
     return SRT_ERR_CUDA;
   }
   int s = srt_assemble(p, S(stream));
@@ -332,6 +403,7 @@ int srt_host_workspace_bytes(srt_plan_t p, int32_t batch, size_t* bytes) {
 static int host_call(srt_plan_t p, int dir, const float* in_h, float* out_h, int32_t batch,
                      void* ws, size_t ws_bytes, void* stream) {
   if (!p || !in_h || !out_h || batch <= 0) return SRT_ERR_ARG;
+  SRT_TRY(check_device(p));
   size_t need = 0;
   srt_host_workspace_bytes(p, batch, &need);
   if (!ws || ((uintptr_t)ws & 255) || ws_bytes < need) return SRT_ERR_WORKSPACE;
@@ -343,15 +415,16 @@ static int host_call(srt_plan_t p, int dir, const float* in_h, float* out_h, int
   float* w0 = dp + align256(np * 4) / 4;
   float* w1 = w0 + align256(buf_elems(g, batch) * 4) / 4;
   cudaStream_t st = S(stream);
-  // results go back in chunks on a copy stream of this call, overlapping the
-  // rest of the transform
+  // results go back in chunks on a copy stream taken from the plan's pool,
+  // overlapping the rest of the transform
+  SrtHostPool::Set cp;
+  SRT_TRY(host_set_take(p, &cp));
   HostSink hs;
   hs.host = out_h;
-  SRT_CUDA_TRY(cudaStreamCreateWithFlags(&hs.cs, cudaStreamNonBlocking));
+  hs.cs = cp.cs;
+  for (int i = 0; i < kHostChunks; ++i) hs.ev[i] = cp.ev[i];
   int s = SRT_OK;
-  for (int i = 0; i < kHostChunks && s == SRT_OK; ++i)
-    if (cudaEventCreateWithFlags(&hs.ev[i], cudaEventDisableTiming) != cudaSuccess) s = SRT_ERR_CUDA;
-  if (s == SRT_OK) {
+  {
     if (dir == 0) {
       s = cudaMemcpyAsync(df, in_h, nf * 4, cudaMemcpyHostToDevice, st) == cudaSuccess
               ? run_forward(p, df, dp, batch, w0, w1, st, &hs)
@@ -362,12 +435,13 @@ static int host_call(srt_plan_t p, int dir, const float* in_h, float* out_h, int
               : SRT_ERR_CUDA;
     }
   }
-  // wait for both streams whatever happened, then release them
-  if (cudaStreamSynchronize(st) != cudaSuccess && s == SRT_OK) s = SRT_ERR_CUDA;
-  if (cudaStreamSynchronize(hs.cs) != cudaSuccess && s == SRT_OK) s = SRT_ERR_CUDA;
-  for (int i = 0; i < kHostChunks; ++i)
-    if (hs.ev[i]) cudaEventDestroy(hs.ev[i]);
-  cudaStreamDestroy(hs.cs);
+  // wait for both streams whatever happened; the copy stream goes back to
+  // the pool only when it finished cleanly
+  const bool ok_st = cudaStreamSynchronize(st) == cudaSuccess;
+  const bool ok_cs = cudaStreamSynchronize(cp.cs) == cudaSuccess;
+  if ((!ok_st || !ok_cs) && s == SRT_OK) s = SRT_ERR_CUDA;
+  if (ok_cs) host_set_give(p, cp);
+  else host_set_destroy(cp);
   return s;
 }
 
@@ -442,6 +516,7 @@ int srt_pipe_create(srt_plan_t p, int32_t batch, int32_t slots, srt_pipe_t* out)
   if (!out) return SRT_ERR_ARG;
   *out = nullptr;
   if (!p || batch <= 0 || slots < 2 || slots > srt_pipe_s::kMaxSlots) return SRT_ERR_ARG;
+  SRT_TRY(check_device(p));
   const srt_geometry& g = p->g;
   const int64_t nf = (int64_t)batch * g.ms * g.ms * g.mz;
   const int64_t np = (int64_t)batch * g.n_phi * g.n_zs * g.n_ell;
@@ -484,6 +559,7 @@ int srt_pipe_create(srt_plan_t p, int32_t batch, int32_t slots, srt_pipe_t* out)
 int srt_pipe_submit(srt_pipe_t q, int32_t direction, const float* in_host, float* out_host,
                     int64_t* ticket) {
   if (!q || !in_host || !out_host || (direction != 0 && direction != 1)) return SRT_ERR_ARG;
+  SRT_TRY(check_device(q->plan));
   const srt_geometry& g = q->plan->g;
   const int64_t nf = (int64_t)q->batch * g.ms * g.ms * g.mz;
   const int64_t np = (int64_t)q->batch * g.n_phi * g.n_zs * g.n_ell;

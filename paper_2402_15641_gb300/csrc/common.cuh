@@ -50,6 +50,8 @@ struct SrtTaps {
   uint16_t* w16 = nullptr;    // nent (SRT_BF16)
 };
 
+struct SrtHostPool;  // copy streams and events of host-buffer calls (api.cu)
+
 struct srt_plan_s {
   srt_geometry g;
   int device = 0;
@@ -65,6 +67,7 @@ struct srt_plan_s {
   int timing = 0;
   cudaEvent_t ev[2][5] = {};
   int have_times[2] = {0, 0};
+  SrtHostPool* host_pool = nullptr;  // created by srt_plan, reused by every host call
 };
 
 // ------------------------------------------------------------- assembly

@@ -50,13 +50,14 @@ def test_clocks_without_nvidia_smi():
 
 
 def test_peaks_measured_and_fallback(tmp_path, monkeypatch):
-    p = bench.peaks()
+    p = bench.peaks(152)
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
         assert p["src"] == "measured"
-    # FP32 FMA peak from 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz
+    # FP32 FMA peak from the device's SMs x 128 lanes x 2 FLOP x 2.07 GHz
     assert p["fp32_tflops"] == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert bench.peaks(148)["fp32_tflops"] == pytest.approx(148 * 128 * 2 * 2.07e9 / 1e12)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    f = bench.peaks()
+    f = bench.peaks(152)
     assert f["src"] == "fallback" and f["hbm_gbs"] == 6800.0
 
 

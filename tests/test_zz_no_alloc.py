@@ -5,8 +5,10 @@ keeps on each GPU instead of a caller workspace.
 
 This file is collected last so that a failure here leaves every other test
 already run.  It checks, through the C ABI, that two calls in a row give the
-same output as srt_forward (within the FP32 tolerance of the other parity
-tests), and that a problem too large for the scratch is refused."""
+same output as srt_forward and srt_adjoint, bit for bit (the same kernels
+run in the same order on the same inputs, so any difference, even one inside
+the FP32 tolerance of the other parity tests, would be a fault), and that a
+problem too large for the scratch is refused."""
 import ctypes
 
 import numpy as np
@@ -15,15 +17,6 @@ import pytest
 from paper_2402_15641_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
-
-FP32_TOL = 1e-5
-
-
-def _rel(a, b):
-    a = a.double().cpu().numpy()
-    b = b.double().cpu().numpy()
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
-
 
 def test_noalloc_forward_matches_forward_twice():
     import torch
@@ -45,7 +38,7 @@ def test_noalloc_forward_matches_forward_twice():
         assert rc == _lib.SRT_OK, (call, rc)
         torch.cuda.synchronize()
         assert torch.isfinite(got).all()
-        assert _rel(got, want) <= FP32_TOL, call
+        assert torch.equal(got, want), call
         y = torch.from_numpy(rng.standard_normal((2, *plan.geom.p_shape)).astype(np.float32)).cuda()
         want_a = plan.adjoint(y)
         got_a = torch.full_like(want_a, float("nan"))
@@ -54,7 +47,7 @@ def test_noalloc_forward_matches_forward_twice():
         assert rc == _lib.SRT_OK, (call, rc)
         torch.cuda.synchronize()
         assert torch.isfinite(got_a).all()
-        assert _rel(got_a, want_a) <= FP32_TOL, call
+        assert torch.equal(got_a, want_a), call
 
 
 def test_noalloc_refuses_problems_larger_than_its_scratch():
