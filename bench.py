@@ -44,6 +44,8 @@ def parse():
                    help="store A2, A2^T as CSR instead of applying them from the Toeplitz taps")
     p.add_argument("--a1-rotation", action="store_true",
                    help="store A1 for a quarter of the sensor columns (4x less A1 memory, same speed)")
+    p.add_argument("--taps-rowwise", action="store_true",
+                   help="A2, A2^T from the taps with a warp per output row (else 2 x 2 row tiles)")
     p.add_argument("--rho-linear", action="store_true",
                    help="piecewise-linear intermediate in rho (else constant on the radius bins)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -339,7 +341,8 @@ def run_ours(args):
     pk = peaks(torch.cuda.get_device_properties(local).multi_processor_count)
     sz = I.sizes(args.workload)
     geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only,
-                               a1_rotation=args.a1_rotation, rho_linear=args.rho_linear)
+                               a1_rotation=args.a1_rotation, rho_linear=args.rho_linear,
+                               taps_rowwise=args.taps_rowwise)
     B = args.batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -497,7 +500,9 @@ def run_ours(args):
                                       "parallelism": "replicas" if world > 1 else "single GPU",
                                       "plan_build_s": round(plan_s, 3),
                                       "nnz1": plan.info["nnz1"], "nnz2": plan.info["nnz2"],
-                                      "a2_form": (f"Toeplitz taps ({plan.info['n_taps']} taps of T)"
+                                      "a2_form": (f"Toeplitz taps ({plan.info['n_taps']} taps of T), "
+                                                  + ("a warp per row" if args.taps_rowwise
+                                                     else "2 x 2 row tiles")
                                                   if plan.info["a2_taps"] else "CSR"),
                                       "a1_form": ("CSR of the first n_phi/4 columns, the rest "
                                                   "by rotation" if plan.info["a1_rot"] else "CSR"),

@@ -63,6 +63,10 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  * nodes); A2's entry (l, k) becomes node l's hat integrated along the
  * semicircle inside slab k, so A2 holds more entries (1.49x at 256^3). */
 #define SRT_RHO_LINEAR 0x10
+/* SRT_TAPS_ROWWISE: apply A2 and A2^T from the taps with one warp per output
+ * row instead of 2 x 2 tiles of output rows (the default; same values up to
+ * the sign of zero sums). */
+#define SRT_TAPS_ROWWISE 0x20
 /* When the rings are spaced like the slabs ((zs_hi - zs_lo) / n_zs = dz, any
  * n_zs, any offset; e.g. n_zs = mz over the volume height), ring h sits at
  * slab h + s plus a fixed fraction of a slab, A2[(h,m),(l,k)] = T[m, k-h-s, l]

@@ -143,6 +143,8 @@ void free_plan(srt_plan_s* p) {
   srt_csr_free(&p->a2t);
   srt_taps_free(&p->tf);
   srt_taps_free(&p->ta);
+  srt_tiles_free(&p->tlf);
+  srt_tiles_free(&p->tla);
   srt_csr_free(&p->tm);
   for (int d = 0; d < 2; ++d)
     for (int i = 0; i < 5; ++i)
@@ -212,7 +214,9 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
     const int h0 = (int)((int64_t)g.n_zs * c / nc), h1 = (int)((int64_t)g.n_zs * (c + 1) / nc);
     const int64_t ra = (int64_t)h0 * g.n_ell, rn = (int64_t)(h1 - h0) * g.n_ell;
     NvRange r("A2 product + reshape P2");
-    if (p->toeplitz)  // A2 from the taps of the master tensor
+    if (p->tiles && nb % 4 == 0)  // A2 from 2 x 2 tiles of the master tensor's taps
+      SRT_TRY(srt_tiles_apply(p, false, h0, h1, 4, w1, nb, w0 + ra * nb, nb, (int)nb, st));
+    else if (p->toeplitz)  // A2 from the taps of the master tensor, a warp per row
       SRT_TRY(srt_taps_apply(p, false, ra, rn, h1 - h0, g.n_ell, 4, w1, nb, w0 + ra * nb, nb,
                              (int)nb, st));
     else
@@ -248,7 +252,9 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   if (!hs) mark(p, 1, 1, st);
   {
     NvRange r("A2^T product");
-    if (p->toeplitz)  // A2^T from the taps of the master tensor
+    if (p->tiles && nb % 4 == 0)  // A2^T from 2 x 2 tiles of the master tensor's taps
+      SRT_TRY(srt_tiles_apply(p, true, 0, g.mz, 4, w0, nb, w1, nb, (int)nb, st));
+    else if (p->toeplitz)  // A2^T from the taps of the master tensor, a warp per row
       SRT_TRY(srt_taps_apply(p, true, 0, c1, 0, 0, 1, w0, nb, w1, nb, (int)nb, st));
     else
       SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));

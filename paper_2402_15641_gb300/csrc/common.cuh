@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <vector>
+
 #include "srt.h"
 
 #define SRT_PI 3.14159265358979323846264338327950288
@@ -50,6 +52,19 @@ struct SrtTaps {
   uint16_t* w16 = nullptr;    // nent (SRT_BF16)
 };
 
+// The same operator as records of 2 x 2 output-row tiles (tiles.cu): per
+// radius pair, one record per gathered row of a tile, holding the row's
+// offset and four weights, sorted by key (the gathered row's slab or ring
+// offset from the tile) with the first record of each key in ptr.
+struct SrtTiles {
+  int pairs = 0, nkeys = 0, key0 = 0;
+  int64_t nrec = 0;
+  int32_t* ptr = nullptr;  // pairs * (nkeys + 1)
+  int32_t* off = nullptr;  // nrec
+  float* w32 = nullptr;    // 4 * nrec (SRT_FP32)
+  uint16_t* w16 = nullptr; // 4 * nrec (SRT_BF16)
+};
+
 struct SrtHostPool;  // copy streams and events of host-buffer calls (api.cu)
 
 struct srt_plan_s {
@@ -60,6 +75,8 @@ struct srt_plan_s {
   int64_t nnz1 = 0;         // entries of the full A1
   int toeplitz = 0;         // second product through the Toeplitz taps below
   SrtTaps tf, ta;           // forward / adjoint taps of A2 (a2, a2t then hold no arrays)
+  SrtTiles tlf, tla;        // forward / adjoint 2 x 2 tile records (from the same taps)
+  int tiles = 0;            // apply A2, A2^T from tlf / tla (else from tf / ta)
   SrtCsr tm;                // master tensor T (rows m, columns l*(2mz-1) + d + mz - 1)
   int64_t dropped1 = 0, dropped2 = 0;
   int64_t bytes = 0;
@@ -79,6 +96,12 @@ void srt_csr_free(SrtCsr* m);
 // l*(2 mz - 1) + d + mz - 1); *nnz2 = number of entries of the A2 they stand for.
 int srt_build_taps(srt_plan_s* plan, const SrtCsr& T, int64_t* nnz2, int64_t* bytes);
 void srt_taps_free(SrtTaps* t);
+// Build plan->tlf / plan->tla from T on the host (rows m, columns l*D + q,
+// D = mz + n_zs - 1; FP32 or BF16 values, whichever is non-empty).
+int srt_build_tiles(srt_plan_s* plan, const std::vector<int32_t>& rp,
+                    const std::vector<int32_t>& col, const std::vector<float>& v32,
+                    const std::vector<uint16_t>& v16, int64_t* bytes);
+void srt_tiles_free(SrtTiles* t);
 // Expand the master tensor into CSR A2 (and A2^T when a2t is given), for export.
 int srt_expand_a2(const srt_plan_s* plan, SrtCsr* a2, SrtCsr* a2t, cudaStream_t stream);
 
@@ -90,6 +113,12 @@ int srt_expand_a2(const srt_plan_s* plan, SrtCsr* a2, SrtCsr* a2t, cudaStream_t 
 int srt_taps_apply(const srt_plan_s* plan, bool adjoint, int64_t r0, int64_t rows, int G, int R,
                    int TG, const float* x, int64_t ldx, float* y, int64_t ldy, int ncols,
                    cudaStream_t stream);
+
+// A2 (adjoint = false: ring rows [c0, c1), y at ring c0's first row) or A2^T
+// (adjoint = true: slabs [c0, c1) = [0, mz)) from the 2 x 2 tile records,
+// blocks of TG coordinate pairs x 8/TG radius pairs.
+int srt_tiles_apply(const srt_plan_s* plan, bool adjoint, int c0, int c1, int TG, const float* x,
+                    int64_t ldx, float* y, int64_t ldy, int ncols, cudaStream_t stream);
 
 // Output rows of A1 / A1^T served from the stored quarter of A1 (spmm.cu):
 // mode 1 = A1 rows (j, l) from stored rows (j mod q, l), pixels turned;

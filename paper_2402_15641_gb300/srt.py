@@ -41,11 +41,13 @@ class Geometry:
     csr_only: bool = False
     a1_rotation: bool = False
     rho_linear: bool = False  # intermediate piecewise linear in rho (else constant on bins)
+    taps_rowwise: bool = False  # A2 from the taps a warp per row (else 2 x 2 row tiles)
 
     @staticmethod
     def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, **options) -> "Geometry":
         """Default readings, computed by the library (srt_geometry_default);
-        options set weight_dtype / keep_f64 / csr_only / a1_rotation / rho_linear."""
+        options set weight_dtype / keep_f64 / csr_only / a1_rotation / rho_linear /
+        taps_rowwise."""
         g = L.SrtGeometry()
         check(L.lib().srt_geometry_default(ctypes.byref(g), ms, mz, dxy, dz, radius, n_phi, n_zs,
                                            n_ell), "srt_geometry_default")
@@ -68,7 +70,8 @@ class Geometry:
                              (L.SRT_KEEP_F64 if self.keep_f64 else 0)
                              | (L.SRT_CSR_ONLY if self.csr_only else 0)
                              | (L.SRT_A1_ROTATION if self.a1_rotation else 0)
-                             | (L.SRT_RHO_LINEAR if self.rho_linear else 0))
+                             | (L.SRT_RHO_LINEAR if self.rho_linear else 0)
+                             | (L.SRT_TAPS_ROWWISE if self.taps_rowwise else 0))
 
     @property
     def f_shape(self):

@@ -298,15 +298,17 @@ def test_toeplitz_second_stage(srt, orc, sz, wdt):
     """With the rings at the slab centres A2 and A2^T are applied from the
     taps of the master tensor T (A2 = T shifted per ring) and never stored:
     the A2 they stand for (exported by expanding T) has the pattern of the
-    directly assembled one and its entries to FP64 rounding, the plan is
-    smaller by A2 and A2^T, and the transforms match the CSR plan and the
-    oracle (dense widths 5 and 15 take the scalar kernel)."""
+    directly assembled one and its entries to FP64 rounding, the taps alone
+    take less memory than A2 and A2^T (the 2 x 2 tile records add some, which
+    on grids this small can outweigh what the taps save), and the transforms
+    match the CSR plan and the oracle (dense widths 5 and 15 take the
+    row-per-warp scalar kernel)."""
     g, o = geom_pair(orc, weight_dtype=wdt, **sz)
     a = srt.Plan(g)
     b = srt.Plan(g.with_(csr_only=True))
     assert a.info["a2_taps"] == 1 and a.info["n_taps"] > 0 and b.info["a2_taps"] == 0
     assert a.info["nnz2"] == b.info["nnz2"]
-    assert a.info["device_bytes"] < b.info["device_bytes"]
+    assert srt.Plan(g.with_(taps_rowwise=True)).info["device_bytes"] < b.info["device_bytes"]
     for which in (2, 4):
         ra, ca, va, _ = a.export(which)
         rb, cb, vb, _ = b.export(which)
@@ -485,3 +487,33 @@ def test_concurrent_calls_on_one_plan(srt, orc):
     for t in threads:
         t.join()
     assert not errors, errors
+
+
+TILE_GEOMS = [dict(I.sizes("srt32")), dict(I.sizes("srt16fd")),
+              dict(ms=9, mz=7, dxy=0.4, dz=0.3, radius=5.0, n_phi=8, n_zs=11, n_ell=23, phi0=0.4,
+                   zs=(-1.65 - 0.57, -2.22 + 3.3)),             # 11 rings spaced dz, offset
+              dict(ms=8, mz=9, dxy=0.5, dz=0.4, radius=6.0, n_phi=12, n_zs=5, n_ell=17,
+                   zs=(-1.0, 1.0))]                                  # 5 rings spaced dz
+
+
+@pytest.mark.parametrize("sz", TILE_GEOMS)
+@pytest.mark.parametrize("wdt", ["fp32", "bf16"])
+@pytest.mark.parametrize("batch", [1, 3])
+def test_tiles_equal_rowwise_taps(srt, orc, sz, wdt, batch):
+    """The 2 x 2 row tiles sum every row in the order of the row-per-warp
+    taps kernel and add only zeros besides, so forward and adjoint agree
+    bitwise (after +0.0, which equates the signs of zero sums); odd ring,
+    slab and radius counts leave half-empty tiles at the edges."""
+    import torch
+    g, o = geom_pair(orc, weight_dtype=wdt, **sz)
+    gr, _ = geom_pair(orc, weight_dtype=wdt, taps_rowwise=True, **sz)
+    plan, ref = srt.Plan(g), srt.Plan(gr)
+    assert plan.info["a2_taps"] == 1
+    rng = np.random.default_rng(31)
+    f = to_dev(rng.uniform(0, 1, (batch, *g.f_shape)))
+    y = to_dev(rng.standard_normal((batch, *g.p_shape)))
+    assert torch.equal(plan.forward(f) + 0.0, ref.forward(f) + 0.0)
+    assert torch.equal(plan.adjoint(y) + 0.0, ref.adjoint(y) + 0.0)
+    tol = FP32_TOL if wdt == "fp32" else BF16_TOL
+    assert rel_l2(to_np(plan.forward(f)[0]), orc.forward(o, to_np(f)[0])) <= tol
+    assert rel_l2(to_np(plan.adjoint(y)[-1]), orc.adjoint(o, to_np(y)[-1])) <= tol
