@@ -80,6 +80,15 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  *     ((i - (ms-1)/2) dxy, (j - (ms-1)/2) dxy, (k - (mz-1)/2) dz).
  *   Sensor columns: (radius cos phi_j, radius sin phi_j), phi_j = phi0 +
  *     2 pi j / n_phi, j < n_phi.  Requires radius > ms*dxy/sqrt(2).
+ *   A block of the columns of a larger aperture (n_phi_total > 0): the plan
+ *     holds columns phi_first .. phi_first + n_phi - 1 of n_phi_total
+ *     equispaced columns, phi_j = phi0 + 2 pi (phi_first + j) / n_phi_total,
+ *     computed exactly as the full aperture's plan computes those columns,
+ *     so its forward is bitwise the full forward's rows of those columns and
+ *     its adjoint is their share of the full adjoint (one A2 serves every
+ *     column, Sec. 2).  Requires 0 <= phi_first, phi_first + n_phi <=
+ *     n_phi_total; n_phi_total = 0 means the whole aperture (n_phi columns).
+ *     SRT_A1_ROTATION needs the whole aperture and is ignored otherwise.
  *   Sensor rings: z_h = zs_lo + (h + 1/2)(zs_hi - zs_lo)/n_zs, h < n_zs.
  *   Radius grid shared by the in-plane radius rho and the shell radius l:
  *     bins [ell_lo + i d, ell_lo + (i+1) d], d = (ell_hi - ell_lo)/n_ell,
@@ -99,6 +108,8 @@ typedef struct srt_geometry {
   double ell_lo, ell_hi;
   int32_t weight_dtype;
   int32_t flags;
+  int32_t n_phi_total;  /* 0, or the aperture's column count when this plan holds a block */
+  int32_t phi_first;    /* first column of the block (0 for the whole aperture) */
 } srt_geometry;
 
 typedef struct srt_plan_s* srt_plan_t;
@@ -120,7 +131,8 @@ typedef struct srt_plan_info_t {
 /*
  * Fill *g with the default readings: rings at the cell centres of the volume
  * height [-mz dz/2, mz dz/2], radius grid [R - r, R + r] with r = ms dxy /
- * sqrt(2) (the in-plane half diagonal), phi0 = 0, FP32 weights, no flags.
+ * sqrt(2) (the in-plane half diagonal), phi0 = 0, FP32 weights, no flags,
+ * the whole aperture (n_phi_total = phi_first = 0).
  * Returns SRT_ERR_ARG for a null g.
  */
 int srt_geometry_default(srt_geometry* g, int32_t ms, int32_t mz, double dxy, double dz,

@@ -30,6 +30,7 @@ class SrtGeometry(ctypes.Structure):
         ("n_zs", ctypes.c_int32), ("zs_lo", ctypes.c_double), ("zs_hi", ctypes.c_double),
         ("n_ell", ctypes.c_int32), ("ell_lo", ctypes.c_double), ("ell_hi", ctypes.c_double),
         ("weight_dtype", ctypes.c_int32), ("flags", ctypes.c_int32),
+        ("n_phi_total", ctypes.c_int32), ("phi_first", ctypes.c_int32),
     ]
 
 

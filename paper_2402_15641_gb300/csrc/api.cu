@@ -43,6 +43,9 @@ int check_geometry(const srt_geometry& g) {
     return SRT_ERR_GEOMETRY;
   if (!(g.radius > g.ms * g.dxy / sqrt(2.0))) return SRT_ERR_GEOMETRY;  // sensors outside
   if (g.weight_dtype != SRT_FP32 && g.weight_dtype != SRT_BF16) return SRT_ERR_GEOMETRY;
+  if (g.n_phi_total < 0 || (g.n_phi_total > 0 && (g.phi_first < 0 ||
+                                                  (int64_t)g.phi_first + g.n_phi > g.n_phi_total)))
+    return SRT_ERR_GEOMETRY;
   // index ranges used in int32 arithmetic by the kernels
   const int64_t pix = (int64_t)g.ms * g.ms, cells = (int64_t)g.n_ell * g.mz;
   const int64_t r1 = (int64_t)g.n_phi * g.n_ell, r2 = (int64_t)g.n_zs * g.n_ell;
@@ -323,6 +326,8 @@ int srt_geometry_default(srt_geometry* g, int32_t ms, int32_t mz, double dxy, do
   g->ell_hi = radius + rxy;
   g->weight_dtype = SRT_FP32;
   g->flags = 0;
+  g->n_phi_total = 0;
+  g->phi_first = 0;
   return SRT_OK;
 }
 

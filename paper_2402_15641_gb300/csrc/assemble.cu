@@ -34,6 +34,7 @@ constexpr unsigned FULL = 0xffffffffu;
 struct GeomDev {
   int ms, mz, n_phi, n_zs, n_ell;
   int nj;       // sensor columns whose A1 rows are assembled (the first nj of n_phi)
+  int jfirst, ntot;  // column j sits at angle phi0 + 2 pi (jfirst + j) / ntot
   int rho_lin;  // A2 columns are hats of the radius nodes (else bins)
   double dxy, dz, radius, phi0, zs_lo, zs_hi, ell_lo, ell_hi;
   double hx, hz, dl, thr1, thr2;
@@ -45,6 +46,8 @@ GeomDev make_geom(const srt_geometry& g) {
   G.mz = g.mz;
   G.n_phi = g.n_phi;
   G.nj = g.n_phi;
+  G.jfirst = g.n_phi_total > 0 ? g.phi_first : 0;
+  G.ntot = g.n_phi_total > 0 ? g.n_phi_total : g.n_phi;
   G.rho_lin = (g.flags & SRT_RHO_LINEAR) ? 1 : 0;
   G.n_zs = g.n_zs;
   G.n_ell = g.n_ell;
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(256) k_assemble(GeomDev G, int rows, int pass,
   const int nstrips = A1 ? G.ms : G.n_ell;
   if (A1) {
     const int j = row / G.n_ell, l = row % G.n_ell;
-    const double phi = G.phi0 + 2.0 * SRT_PI * j / G.n_phi;
+    const double phi = G.phi0 + 2.0 * SRT_PI * (G.jfirst + j) / G.ntot;
     cu = G.radius * cos(phi);  // x of the sensor column (strip axis)
     cv = G.radius * sin(phi);  // y
     r = G.ell_lo + (l + 0.5) * G.dl;
@@ -560,7 +563,10 @@ int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
   // pixel grid turned by 90 degrees about the axis, so the rows of the first
   // n_phi/4 columns determine all of A1 (and A1^T)
   GeomDev G1 = G;
-  if ((plan->g.flags & SRT_A1_ROTATION) && plan->g.n_phi % 4 == 0 && plan->g.ms < 4096) {
+  const bool full_circle = plan->g.n_phi_total <= 0 ||
+                           (plan->g.n_phi_total == plan->g.n_phi && plan->g.phi_first == 0);
+  if ((plan->g.flags & SRT_A1_ROTATION) && full_circle && plan->g.n_phi % 4 == 0 &&
+      plan->g.ms < 4096) {
     G1.nj = plan->g.n_phi / 4;
     plan->a1_rot = 1;
   }

@@ -42,6 +42,8 @@ class Geometry:
     a1_rotation: bool = False
     rho_linear: bool = False  # intermediate piecewise linear in rho (else constant on bins)
     taps_rowwise: bool = False  # A2 from the taps a warp per row (else 2 x 2 row tiles)
+    n_phi_total: int = 0  # > 0: the plan holds columns phi_first .. + n_phi - 1 of this many
+    phi_first: int = 0
 
     @staticmethod
     def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, **options) -> "Geometry":
@@ -62,6 +64,12 @@ class Geometry:
     def with_(self, **kw) -> "Geometry":
         return replace(self, **kw)
 
+    def column_block(self, j0: int, j1: int) -> "Geometry":
+        """The plan geometry of sensor columns j0 .. j1-1 of this aperture."""
+        if not 0 <= j0 < j1 <= self.n_phi or self.n_phi_total:
+            raise ValueError(f"column block [{j0}, {j1}) of {self.n_phi} columns")
+        return replace(self, n_phi=j1 - j0, n_phi_total=self.n_phi, phi_first=j0)
+
     def to_c(self) -> L.SrtGeometry:
         wd = {"fp32": L.SRT_FP32, "bf16": L.SRT_BF16}[self.weight_dtype]
         return L.SrtGeometry(self.ms, self.mz, self.dxy, self.dz, self.radius, self.n_phi,
@@ -71,7 +79,8 @@ class Geometry:
                              | (L.SRT_CSR_ONLY if self.csr_only else 0)
                              | (L.SRT_A1_ROTATION if self.a1_rotation else 0)
                              | (L.SRT_RHO_LINEAR if self.rho_linear else 0)
-                             | (L.SRT_TAPS_ROWWISE if self.taps_rowwise else 0))
+                             | (L.SRT_TAPS_ROWWISE if self.taps_rowwise else 0),
+                             self.n_phi_total, self.phi_first)
 
     @property
     def f_shape(self):
