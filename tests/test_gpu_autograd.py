@@ -91,3 +91,53 @@ def test_least_squares_128(mods, orc):
     v = to_dev(np.random.default_rng(9).standard_normal(g.f_shape))
     rq = S.dot_f64(plan.forward(v), plan.forward(v)) / S.dot_f64(v, v)
     assert rq <= res.lipschitz * (1 + 1e-3)
+
+
+class _Interrupted:
+    """A real plan whose calls raise on the host after `fail_after` calls,
+    before any further launch: the run stops between steps with nothing of
+    its own in flight (the injected failure of a checkpoint / resume test)."""
+
+    def __init__(self, plan, fail_after=None):
+        self.plan, self.geom, self.device = plan, plan.geom, plan.device
+        self.calls, self.fail_after = 0, fail_after
+
+    def _tick(self):
+        self.calls += 1
+        if self.fail_after is not None and self.calls > self.fail_after:
+            raise RuntimeError("injected failure")
+
+    def forward(self, f, **kw):
+        self._tick()
+        return self.plan.forward(f, **kw)
+
+    def adjoint(self, p, **kw):
+        self._tick()
+        return self.plan.adjoint(p, **kw)
+
+
+def test_least_squares_resumes_bitwise_on_gpu(mods, orc, tmp_path):
+    """Least squares on the 32^3 geometry with a checkpoint every 3
+    iterations: a run stopped by a host-side failure in iteration 8 and
+    resumed from its iteration-6 checkpoint computes the same iterates and
+    losses, bit for bit, as a run that was never interrupted (the products
+    hold no atomics; the iterate is saved exactly)."""
+    import torch
+    S, A = mods
+    g, _ = geom_pair(orc, **dict(I.sizes("srt32")))
+    plan = S.Plan(g)
+    p = plan.forward(to_dev(I.phantom("srt32")))
+    ref = A.least_squares(plan, p, iters=12, reg=1e-3)
+    ck = str(tmp_path / "lsq32.pt")
+    # 20 power-iteration calls (forward + adjoint each) and 2 per iteration:
+    # the 8th iteration's first call fails
+    with pytest.raises(RuntimeError, match="injected"):
+        A.least_squares(_Interrupted(plan, fail_after=40 + 2 * 7), p, iters=12, reg=1e-3,
+                        checkpoint=ck, every=3)
+    st = torch.load(ck, weights_only=True)
+    assert st["iter"] == 6 and len(st["losses"]) == 6
+    again = _Interrupted(plan)
+    res = A.least_squares(again, p, iters=12, reg=1e-3, checkpoint=ck, every=3)
+    assert again.calls == 2 * 6 + 1  # resumed at iteration 7: no power iterations
+    assert torch.equal(res.f, ref.f)
+    assert res.losses == ref.losses and res.step == ref.step

@@ -125,3 +125,60 @@ def test_poisson_run_reports_latency(env):
     assert s["n"] == len(reqs) > 100
     assert 0 < s["p50_ms"] <= s["p99_ms"]
     srv.close()
+
+
+_SIZES = {"a": (16, 32), "b": (24, 48), "c": (20, 40)}
+
+
+@pytest.mark.parametrize("wdt,tol", [("fp32", 1e-5), ("bf16", 5e-3)])
+def test_served_results_match_the_oracle(env, orc, wdt, tol):
+    """Every forward and adjoint served in a mixed run of the three test
+    geometries, against the FP64 oracle in full (relative L2 <= 1e-5 with
+    FP32 entries, <= 5e-3 with BF16 entries)."""
+    SV, Plan, geoms, payloads = env
+    geoms = {k: g.with_(weight_dtype=wdt) for k, g in geoms.items()}
+    srv = SV.Server(geoms, budget_bytes=8 << 30, max_batch=16, n_streams=3)
+    reqs = [srv.submit(k, d, payloads[(k, d)][i]) for i in range(2) for d in ("fwd", "adj")
+            for k in "abc"]
+    srv.drain()
+    for r in reqs:
+        o = orc.OracleGeometry.default(**I.sizes(I.serving_geometry(*_SIZES[r.key])))
+        x = r.payload.double().numpy()
+        want = orc.forward(o, x) if r.direction == "fwd" else orc.adjoint(o, x)
+        got = r.result.double().numpy()
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        assert err <= tol, (r.key, r.direction, err)
+    srv.close()
+
+
+@pytest.mark.parametrize("edge,n_phi", [(64, 128), (128, 256)])
+def test_serving_mix_geometries_against_the_oracle(env, orc, edge, n_phi):
+    """Geometries of the serving mix itself (64^3 / 128 columns and 128^3 /
+    256 columns, FP32 entries), served as batches of two: forward values on
+    256 seeded shells and adjoint values on 12 seeded voxels against the
+    FP64 oracle (relative L2 <= 1e-5)."""
+    SV, Plan, _, _ = env
+    from paper_2402_15641_gb300.srt import Geometry
+    sz = I.sizes(I.serving_geometry(edge, n_phi))
+    geoms = {"m": Geometry.from_sizes(sz)}
+    pl = SV.make_payloads(geoms, per=2, seed=11)
+    srv = SV.Server(geoms, budget_bytes=16 << 30, max_batch=16, n_streams=2)
+    reqs = [srv.submit("m", d, pl[("m", d)][i]) for d in ("fwd", "adj") for i in range(2)]
+    srv.drain()
+    o = orc.OracleGeometry.default(**sz)
+    rng = np.random.default_rng(edge)
+    sh = np.stack([rng.integers(0, n, 256) for n in o.p_shape], axis=1)
+    vx = np.stack([rng.integers(0, n, 12) for n in o.f_shape], axis=1)
+    for r in reqs:
+        x = r.payload.double().numpy()
+        got = r.result.double().numpy()
+        if r.direction == "fwd":
+            want = orc.forward_shells(o, x, sh)
+            have = got[sh[:, 0], sh[:, 1], sh[:, 2]]
+        else:
+            want = orc.adjoint_voxels(o, x, vx)
+            have = got[vx[:, 0], vx[:, 1], vx[:, 2]]
+        err = float(np.linalg.norm(have - want) / np.linalg.norm(want))
+        print(f"PARITY serving {edge}^3/{n_phi} {r.direction}: rel-L2 {err:.2e}")
+        assert err <= 1e-5, (r.direction, err)
+    srv.close()
