@@ -43,9 +43,11 @@ def parse():
     p.add_argument("--csr-only", action="store_true",
                    help="store A2, A2^T as CSR instead of applying them from the Toeplitz taps")
     p.add_argument("--a1-rotation", action="store_true",
-                   help="store A1 for a quarter of the sensor columns (4x less A1 memory, same speed)")
-    p.add_argument("--taps-rowwise", action="store_true",
-                   help="A2, A2^T from the taps with a warp per output row (else 2 x 2 row tiles)")
+                   help="store A1 for a quarter of the sensor columns (quarter turns only, no mirror)")
+    p.add_argument("--rowwise", action="store_true",
+                   help="every product a warp per output row (else register tiles of rows)")
+    p.add_argument("--a1-full", action="store_true",
+                   help="store A1 for every sensor column (else for the aperture's symmetry set)")
     p.add_argument("--rho-linear", action="store_true",
                    help="piecewise-linear intermediate in rho (else constant on the radius bins)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -169,12 +171,11 @@ def stage_model(geom, info, batch, weights):
     y1 = 4 * batch * r1 * geom.mz           # bytes of Y1 (= Y1')
     pp = 4 * batch * r2 * geom.n_phi        # bytes of P' (= p)
     fv = 4 * batch * pix * geom.mz          # bytes of f
-    if info.get("a1_rot"):  # a quarter of A1 (and of A1^T) is stored; the rest by rotation
-        a1b = nnz1 // 4 * (vb + 4) + 4 * (r1 // 4 + 1)
-        a1tb = nnz1 // 4 * (vb + 4) + 4 * (pix + 1)
-    else:
-        a1b = nnz1 * (vb + 4) + 4 * (r1 + 1)
-        a1tb = nnz1 * (vb + 4) + 4 * (pix + 1)
+    # A1 (and A1^T) stored for a fundamental set of columns: a quarter under
+    # quarter turns, an eighth (n_phi/8 + 1 of n_phi columns) with the mirror
+    frac = {1: 1 / 4, 2: (geom.n_phi // 8 + 1) / geom.n_phi}.get(info.get("a1_rot", 0), 1.0)
+    a1b = int(nnz1 * frac) * (vb + 4) + 4 * (int(r1 * frac) + 1)
+    a1tb = int(nnz1 * frac) * (vb + 4) + 4 * (pix + 1)
     spmm1 = dict(flop=2 * nnz1 * geom.mz * batch, bytes=a1b + fv + y1)
     if info.get("a2_taps"):  # A2 held by the taps of T: key + value per tap, sub-row pointers
         sub = 4 * (geom.n_ell * (2 * geom.mz - 1) + 1)
@@ -342,7 +343,7 @@ def run_ours(args):
     sz = I.sizes(args.workload)
     geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only,
                                a1_rotation=args.a1_rotation, rho_linear=args.rho_linear,
-                               taps_rowwise=args.taps_rowwise)
+                               rowwise=args.rowwise, a1_full=args.a1_full)
     B = args.batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -501,11 +502,16 @@ def run_ours(args):
                                       "plan_build_s": round(plan_s, 3),
                                       "nnz1": plan.info["nnz1"], "nnz2": plan.info["nnz2"],
                                       "a2_form": (f"Toeplitz taps ({plan.info['n_taps']} taps of T), "
-                                                  + ("a warp per row" if args.taps_rowwise
+                                                  + ("a warp per row" if args.rowwise
                                                      else "2 x 2 row tiles")
                                                   if plan.info["a2_taps"] else "CSR"),
-                                      "a1_form": ("CSR of the first n_phi/4 columns, the rest "
-                                                  "by rotation" if plan.info["a1_rot"] else "CSR"),
+                                      "a1_form": {0: "every column", 1: "the first n_phi/4 "
+                                                  "columns, the rest by quarter turns",
+                                                  2: "the first n_phi/8 + 1 columns, the rest by "
+                                                  "quarter turns and the diagonal mirror"}[
+                                                      plan.info["a1_rot"]]
+                                                  + ("; a warp per row" if args.rowwise
+                                                     else "; 4-radius and 2 x 2-pixel row tiles"),
                                       "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3),
                                       "intermediate": ("piecewise linear in rho" if args.rho_linear
                                                        else "piecewise constant on radius bins")}),

@@ -48,12 +48,12 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
 /* Plan flags. */
 #define SRT_KEEP_F64 0x1 /* keep FP64 copies of A1/A2 entries for srt_plan_export */
 #define SRT_CSR_ONLY 0x2 /* store A2, A2^T as CSR even when the taps would serve   */
-/* SRT_A1_ROTATION: with n_phi a multiple of 4 (and ms < 4096), store A1 and
- * A1^T for the first n_phi/4 sensor columns only: column j + n_phi/4 sees the
- * pixel grid turned by 90 degrees, A1[(j + n_phi/4, l), rot(p)] = A1[(j, l), p]
- * with rot(ix, iy) = (ms-1-iy, ix).  A1's memory drops 4x, at the speed of
- * the stored form (within 0.5% at 256^3; srt_plan_info_t.a1_rot reports it).
- * Ignored where n_phi % 4 != 0 or ms >= 4096. */
+/* SRT_A1_ROTATION: use the quarter turns only (n_phi % 4 == 0, ms < 4096):
+ * store A1 and A1^T for the first n_phi/4 sensor columns; column j + n_phi/4
+ * sees the pixel grid turned by 90 degrees, A1[(j + n_phi/4, l), rot(p)] =
+ * A1[(j, l), p] with rot(ix, iy) = (ms-1-iy, ix).  The 8-fold form adds the
+ * mirror across the diagonal (ix, iy) -> (iy, ix), which takes column t to
+ * n_phi/4 - t (see SRT_A1_FULL for when each form applies). */
 #define SRT_A1_ROTATION 0x8
 /* SRT_RHO_LINEAR: the intermediate f^{1,2} is piecewise linear in rho instead
  * of constant on the radius bins (Sec. 3.1 notes the method carries over to
@@ -63,10 +63,20 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  * nodes); A2's entry (l, k) becomes node l's hat integrated along the
  * semicircle inside slab k, so A2 holds more entries (1.49x at 256^3). */
 #define SRT_RHO_LINEAR 0x10
-/* SRT_TAPS_ROWWISE: apply A2 and A2^T from the taps with one warp per output
- * row instead of 2 x 2 tiles of output rows (the default; same values up to
- * the sign of zero sums). */
-#define SRT_TAPS_ROWWISE 0x20
+/* SRT_ROWWISE: apply every product with one warp per output row (CSR rows,
+ * or A2's taps) instead of register tiles of output rows (the default).  A
+ * row then sums its entries in ascending column order: with A1 stored for
+ * every column the tiled and the row-wise forms agree bitwise (up to the
+ * sign of zero sums); with the symmetric forms the order differs. */
+#define SRT_ROWWISE 0x20
+/* SRT_A1_FULL: store A1 and A1^T for every sensor column.  By default the
+ * plan stores A1 for a fundamental set of columns of the aperture's
+ * symmetry (srt_plan_info_t.a1_rot): the first n_phi/8 + 1 columns under
+ * quarter turns and the mirror across the diagonal (n_phi % 8 == 0,
+ * phi0 = 0, the whole aperture, ms even, mz % 4 == 0), else the first
+ * n_phi/4 under quarter turns (n_phi % 4 == 0, the whole aperture), else
+ * every column. */
+#define SRT_A1_FULL 0x40
 /* When the rings are spaced like the slabs ((zs_hi - zs_lo) / n_zs = dz, any
  * n_zs, any offset; e.g. n_zs = mz over the volume height), ring h sits at
  * slab h + s plus a fixed fraction of a slab, A2[(h,m),(l,k)] = T[m, k-h-s, l]
@@ -124,7 +134,9 @@ typedef struct srt_plan_info_t {
   int32_t a2_taps;            /* 1: A2, A2^T applied from Toeplitz taps       */
   int64_t n_taps;             /* taps of the master tensor T (0 for CSR A2)   */
   int32_t a1_rot;             /* 1: only the first n_phi/4 columns of A1 are  */
-                              /*    stored; the rest follow by rotation       */
+                              /*    stored, the rest follow by quarter turns; */
+                              /* 2: the first n_phi/8 + 1, by quarter turns   */
+                              /*    and the diagonal mirror; 0: every column  */
   int32_t reserved;
 } srt_plan_info_t;
 

@@ -18,7 +18,8 @@ SRT_KEEP_F64 = 1
 SRT_CSR_ONLY = 2
 SRT_A1_ROTATION = 8
 SRT_RHO_LINEAR = 16
-SRT_TAPS_ROWWISE = 32
+SRT_ROWWISE = 32
+SRT_A1_FULL = 64
 SRT_NOALLOC_WORKSPACE_BYTES = 32 << 20
 
 

@@ -148,6 +148,7 @@ void free_plan(srt_plan_s* p) {
   srt_taps_free(&p->ta);
   srt_tiles_free(&p->tlf);
   srt_tiles_free(&p->tla);
+  srt_a1tiles_free(&p->a1tl);
   srt_csr_free(&p->tm);
   for (int d = 0; d < 2; ++d)
     for (int i = 0; i < 5; ++i)
@@ -167,6 +168,7 @@ SrtRot a1_rot(const srt_plan_s* p, int mode) {
     r.ms = p->g.ms;
     r.n_ell = p->g.n_ell;
     r.q = p->g.n_phi / 4;
+    r.mirror = p->a1_rot == 2 ? 1 : 0;
   }
   return r;
 }
@@ -199,6 +201,12 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   // rows (j, l) visited radius-chunk-major across sensor columns (L2 reuse of F)
   {
     NvRange r("A1 product");
+    // CSR rows, a warp per row: the 8 warps of a block take 8 consecutive
+    // radii of one column, whose circles cross the same pixels, and share
+    // those gathers in L1 (46% hits).  4-radius register tiles
+    // (srt_a1tiles_apply) fetch each pixel once per tile instead, but lose
+    // that sharing (13% L1 hits) and measured slower (1.74-1.97 against
+    // 1.56 ms at 256^3).
     SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B,
                      st, g.n_phi, g.n_ell, 1, 0, r1, a1_rot(p, 1)));
   }
@@ -273,13 +281,20 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   // tile touches more of its pixels than of a line of 8, so warps share L1;
   // blocks walk 64 x 64 pixel super-tiles (where the grid divides), so the
   // rows gathered at any time stay within what L2 holds (2% faster at 256^3)
-  const int nc = hs ? (g.ms < hs->chunks ? g.ms : hs->chunks) : 1;
+  // (tiles: 2 x 2 pixel tiles, chunks of whole tile rows)
+  const int span = p->a1tiles ? g.ms / 2 : g.ms;
+  const int nc = hs ? (span < hs->chunks ? span : hs->chunks) : 1;
   for (int c = 0; c < nc; ++c) {
-    const int x0 = (int)((int64_t)g.ms * c / nc), x1 = (int)((int64_t)g.ms * (c + 1) / nc);
+    const int t0 = (int)((int64_t)span * c / nc), t1 = (int)((int64_t)span * (c + 1) / nc);
+    const int x0 = p->a1tiles ? 2 * t0 : t0, x1 = p->a1tiles ? 2 * t1 : t1;
     const int64_t ra = (int64_t)x0 * g.ms, rn = (int64_t)(x1 - x0) * g.ms;
     NvRange r("A1^T product");
-    SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f + ra * g.mz, g.mz,
-                     pix * g.mz, g.mz, B, st, x1 - x0, g.ms, 4, ra, rn, a1_rot(p, 2), 64));
+    if (p->a1tiles)
+      SRT_TRY(srt_a1tiles_apply(p, t0, t1, f1, g.mz, r1 * g.mz, f + ra * g.mz, g.mz,
+                                pix * g.mz, g.mz, B, st));
+    else
+      SRT_TRY(srt_spmm(p->a1t, g.weight_dtype, f1, g.mz, r1 * g.mz, f + ra * g.mz, g.mz,
+                       pix * g.mz, g.mz, B, st, x1 - x0, g.ms, 4, ra, rn, a1_rot(p, 2), 64));
     if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra * g.mz, f + ra * g.mz, rn * g.mz, pix * g.mz, B));
   }
   if (hs) return SRT_OK;
@@ -699,7 +714,7 @@ int export_a1_rot(const srt_plan_s* p, bool transpose, int32_t* rowptr, int32_t*
   const SrtCsr& m = p->a1;
   const srt_geometry& g = p->g;
   if (val64 && !m.v64) return SRT_ERR_ARG;
-  const int q = g.n_phi / 4, ms = g.ms, ne = g.n_ell;
+  const int q = g.n_phi / 4, ms = g.ms, ne = g.n_ell, mode = p->a1_rot;
   const int64_t ns = m.nnz, rows = (int64_t)g.n_phi * ne, pix = (int64_t)ms * ms;
   std::vector<int32_t> rp(m.rows + 1), cl(ns);
   std::vector<float> v(ns);
@@ -719,27 +734,34 @@ int export_a1_rot(const srt_plan_s* p, bool transpose, int32_t* rowptr, int32_t*
     }
     if (val64) SRT_CUDA_TRY(cudaMemcpy(v64.data(), m.v64, ns * 8, cudaMemcpyDeviceToHost));
   }
-  auto turn = [ms](int pp, int s) {
-    const int ix = pp / ms, iy = pp - ix * ms;
+  // pixel pp under s quarter turns after the diagonal mirror when m
+  auto turn = [ms](int pp, int s, int m) {
+    int ix = pp / ms, iy = pp - ix * ms;
+    if (m) std::swap(ix, iy);
     switch (s & 3) {
-      case 0: return pp;
+      case 0: return ix * ms + iy;
       case 1: return (ms - 1 - iy) * ms + ix;
       case 2: return (ms - 1 - ix) * ms + (ms - 1 - iy);
       default: return iy * ms + (ms - 1 - ix);
     }
   };
   // full A1, rows sorted by column
-  std::vector<int32_t> frp(rows + 1), fcl(4 * ns);
-  std::vector<float> fv(4 * ns);
-  std::vector<double> f64(val64 ? 4 * ns : 0);
+  std::vector<int32_t> frp(rows + 1), fcl(8 * ns);
+  std::vector<float> fv(8 * ns);
+  std::vector<double> f64(val64 ? 8 * ns : 0);
   std::vector<std::pair<int32_t, int64_t>> tmp;
   int64_t at = 0;
   for (int64_t r = 0; r < rows; ++r) {
     frp[r] = (int32_t)at;
-    const int j = (int)(r / ne), l = (int)(r % ne), s = j / q;
-    const int64_t sr = (int64_t)(j % q) * ne + l;
+    const int jj = (int)(r / ne), l = (int)(r % ne), s = jj / q;
+    int j = jj % q, m = 0;
+    if (mode == 2 && 2 * j > q) {  // column s q + t is stored column q - t, mirrored
+      j = q - j;
+      m = 1;
+    }
+    const int64_t sr = (int64_t)j * ne + l;
     tmp.clear();
-    for (int64_t e = rp[sr]; e < rp[sr + 1]; ++e) tmp.emplace_back(turn(cl[e], s), e);
+    for (int64_t e = rp[sr]; e < rp[sr + 1]; ++e) tmp.emplace_back(turn(cl[e], s, m), e);
     std::sort(tmp.begin(), tmp.end());
     for (auto& t : tmp) {
       fcl[at] = t.first;

@@ -24,6 +24,8 @@
 // count pass and the fill pass run the same enumeration, so they agree.
 #include <string.h>
 
+#include <vector>
+
 #include "common.cuh"
 #include "devutil.cuh"
 
@@ -562,18 +564,45 @@ int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
   // A1 by rotation: with n_phi a multiple of 4, column j + n_phi/4 sees the
   // pixel grid turned by 90 degrees about the axis, so the rows of the first
   // n_phi/4 columns determine all of A1 (and A1^T)
+  // (and the mirror across the diagonal takes column t to n_phi/4 - t, so
+  // with n_phi a multiple of 8 and phi0 = 0 the first n_phi/8 + 1 do).
+  // The 8-fold form is applied by the tile kernels only (a1tiles.cu).
+  const srt_geometry& g0 = plan->g;
+  const int fl = g0.flags;
+  const bool full_circle =
+      g0.n_phi_total <= 0 || (g0.n_phi_total == g0.n_phi && g0.phi_first == 0);
+  const bool tiles = g0.ms % 2 == 0 && g0.ms < 4096 && g0.mz % 4 == 0 && g0.n_phi < 32768 &&
+                     g0.n_ell < 65536 && !(fl & SRT_ROWWISE);
   GeomDev G1 = G;
-  const bool full_circle = plan->g.n_phi_total <= 0 ||
-                           (plan->g.n_phi_total == plan->g.n_phi && plan->g.phi_first == 0);
-  if ((plan->g.flags & SRT_A1_ROTATION) && full_circle && plan->g.n_phi % 4 == 0 &&
-      plan->g.ms < 4096) {
-    G1.nj = plan->g.n_phi / 4;
-    plan->a1_rot = 1;
+  if (!(fl & SRT_A1_FULL) && full_circle && g0.n_phi % 4 == 0 && g0.ms < 4096) {
+    if (tiles && g0.n_phi % 8 == 0 && g0.phi0 == 0.0 && !(fl & SRT_A1_ROTATION)) {
+      G1.nj = g0.n_phi / 8 + 1;
+      plan->a1_rot = 2;
+    } else {
+      G1.nj = g0.n_phi / 4;
+      plan->a1_rot = 1;
+    }
   }
   SRT_TRY(assemble_one<true>(G1, wdt, &plan->a1, &plan->dropped1, &plan->bytes, st));
-  const int64_t copies = plan->a1_rot ? 4 : 1;
-  plan->nnz1 = plan->a1.nnz * copies;
-  plan->dropped1 *= copies;
+  if (plan->a1_rot == 2) {
+    // columns 0 and n_phi/8 have 4 images, the others 8
+    const int ne = g0.n_ell, half = g0.n_phi / 8;
+    std::vector<int32_t> rp(plan->a1.rows + 1);
+    SRT_CUDA_TRY(cudaMemcpy(rp.data(), plan->a1.rowptr, rp.size() * 4, cudaMemcpyDeviceToHost));
+    int64_t n = 0;
+    for (int j = 0; j <= half; ++j)
+      n += (int64_t)(rp[(j + 1) * ne] - rp[j * ne]) * ((j == 0 || j == half) ? 4 : 8);
+    plan->nnz1 = n;
+    plan->dropped1 *= 8;  // an upper bound: the drops are not counted per column
+  } else {
+    const int64_t copies = plan->a1_rot ? 4 : 1;
+    plan->nnz1 = plan->a1.nnz * copies;
+    plan->dropped1 *= copies;
+  }
+  if (tiles) {
+    SRT_TRY(srt_build_a1tiles(plan, &plan->bytes));
+    plan->a1tiles = 1;
+  }
   if (toeplitz_applies(plan->g)) {
     // master tensor: one ring over D = mz + n_zs - 1 slabs, slab q at offset
     // d = q + dmin from it, dmin = -(n_zs - 1) - s, where the ring range
@@ -615,7 +644,8 @@ int srt_assemble(srt_plan_s* plan, cudaStream_t st) {
   } else {
     plan->bytes += (plan->a1.nnz + (plan->toeplitz ? 0 : plan->a2.nnz)) * (int64_t)sizeof(double);
   }
-  SRT_TRY(transpose_csr(plan->a1, &plan->a1t, &plan->bytes, st));
+  // (the 8-fold form's A1^T runs from the tile records only)
+  if (plan->a1_rot != 2) SRT_TRY(transpose_csr(plan->a1, &plan->a1t, &plan->bytes, st));
   if (!plan->toeplitz) SRT_TRY(transpose_csr(plan->a2, &plan->a2t, &plan->bytes, st));
   return SRT_OK;
 }

@@ -65,13 +65,28 @@ struct SrtTiles {
   uint16_t* w16 = nullptr; // 4 * nrec (SRT_BF16)
 };
 
+// A1^T as records of 2 x 2 pixel tiles (a1tiles.cu): key = (j << 16 | l),
+// four weights per record, two lists per tile (aptr[2t] .. aptr[2t+1]: read
+// by every symmetry pass; .. aptr[2t+2]: by the unmirrored passes only).
+struct SrtA1Tiles {
+  int ntx = 0;
+  int64_t na = 0;
+  int32_t* aptr = nullptr;  // 2 * ntx^2 + 1
+  int32_t* akey = nullptr;  // na
+  float* aw32 = nullptr;    // 4 * na (SRT_FP32)
+  uint16_t* aw16 = nullptr; // 4 * na (SRT_BF16)
+};
+
 struct SrtHostPool;  // copy streams and events of host-buffer calls (api.cu)
 
 struct srt_plan_s {
   srt_geometry g;
   int device = 0;
   SrtCsr a1, a2, a1t, a2t;  // A1 = A^{1,2}, A2 = A^{3,4} and their transposes
-  int a1_rot = 0;           // a1, a1t hold the first n_phi/4 sensor columns only
+  int a1_rot = 0;           // 1: a1, a1t hold the first n_phi/4 sensor columns (4-fold
+                            // rotation); 2: the first n_phi/8 + 1 (rotation and mirror)
+  SrtA1Tiles a1tl;          // A1^T tile records (a1tiles.cu)
+  int a1tiles = 0;          // apply A1^T from a1tl
   int64_t nnz1 = 0;         // entries of the full A1
   int toeplitz = 0;         // second product through the Toeplitz taps below
   SrtTaps tf, ta;           // forward / adjoint taps of A2 (a2, a2t then hold no arrays)
@@ -120,13 +135,25 @@ int srt_taps_apply(const srt_plan_s* plan, bool adjoint, int64_t r0, int64_t row
 int srt_tiles_apply(const srt_plan_s* plan, bool adjoint, int c0, int c1, int TG, const float* x,
                     int64_t ldx, float* y, int64_t ldy, int ncols, cudaStream_t stream);
 
+// A1^T tile records from the plan's stored A1 (CSR on the device).
+int srt_build_a1tiles(srt_plan_s* plan, int64_t* bytes);
+void srt_a1tiles_free(SrtA1Tiles* t);
+// A1^T from the tile records: 2 x 2 pixel tiles of pixel rows 2 g0 .. 2 g1 - 1,
+// y at pixel row 2 g0; batch items b at x + b bsx, y + b bsy.
+int srt_a1tiles_apply(const srt_plan_s* plan, int g0, int g1, const float* x, int64_t ldx,
+                      int64_t bsx, float* y, int64_t ldy, int64_t bsy, int ncols, int batch,
+                      cudaStream_t stream);
+
 // Output rows of A1 / A1^T served from the stored quarter of A1 (spmm.cu):
-// mode 1 = A1 rows (j, l) from stored rows (j mod q, l), pixels turned;
+// mode 1 = A1 rows (j, l) from stored rows (j mod q, l), pixels turned (with
+// mirror: column s q + t from stored column q - t for t > q/2, pixels
+// mirrored across the diagonal first);
 // mode 2 = A1^T rows (pixels) from 4 stored rows of the stored transpose.
 struct SrtRot {
   int mode = 0;           // 0: rows are stored as they are
   int ms = 0, n_ell = 0;  // pixel grid edge, radius bins
-  int q = 0;              // stored sensor columns (n_phi / 4)
+  int q = 0;              // n_phi / 4
+  int mirror = 0;         // mode 1 only: the 8-fold form (stored columns 0 .. q/2)
 };
 
 // y[b][r - r0][n] = sum_e A[r, col[e]] * x[b][col[e]][n] for output rows

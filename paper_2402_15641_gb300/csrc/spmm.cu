@@ -36,8 +36,14 @@ __device__ __forceinline__ float wval<uint16_t>(uint16_t v) {
 // Pixel p = ix*ms + iy turned s quarter turns: rot(ix, iy) = (ms-1-iy, ix).
 // ix = floor(p / ms) as (p * magic) >> 40 with magic = ceil(2^40 / ms), exact
 // for p < 2^24 and ms < 2^16 (the quotient's error stays below 1/ms).
-__device__ __forceinline__ int rot_pixel(int p, int s, int ms, uint64_t magic) {
-  const int ix = (int)(((uint64_t)(uint32_t)p * magic) >> 40), iy = p - ix * ms;
+__device__ __forceinline__ int rot_pixel(int p, int s, int ms, uint64_t magic, bool m = false) {
+  int ix = (int)(((uint64_t)(uint32_t)p * magic) >> 40), iy = p - ix * ms;
+  if (m) {  // mirror across the diagonal first: (ix, iy) -> (iy, ix)
+    const int t = ix;
+    ix = iy;
+    iy = t;
+    p = ix * ms + iy;
+  }
   switch (s & 3) {
     case 0: return p;
     case 1: return (ms - 1 - iy) * ms + ix;
@@ -87,19 +93,25 @@ struct Rows {
 };
 
 // Stored row and gathered-row remap of segment s of output row `row`.
+// Mode 1, the 8-fold form: is output column j served by a mirrored column?
+__device__ __forceinline__ bool seg_mirrored(const Rows& A, int j) {
+  return A.rot.mirror && 2 * (j % A.rot.q) > A.rot.q;
+}
 template <int MODE>
 __device__ __forceinline__ int seg_row(const Rows& A, int row, int s) {
   if (MODE == 1) {
     const int j = row / A.rot.n_ell, l = row - j * A.rot.n_ell;
-    return (j % A.rot.q) * A.rot.n_ell + l;
+    const int js = j % A.rot.q;
+    return (seg_mirrored(A, j) ? A.rot.q - js : js) * A.rot.n_ell + l;
   }
   if (MODE == 2) return rot_pixel(row, 4 - s, A.rot.ms, A.magic);
   return row;
 }
-// Gathered row of stored column c in segment s (t: quarter turns of the row).
+// Gathered row of stored column c in segment s (t: quarter turns of the row,
+// mir: mirrored first).
 template <int MODE>
-__device__ __forceinline__ int seg_col(const Rows& A, int t, int s, int c) {
-  if (MODE == 1) return rot_pixel(c, t, A.rot.ms, A.magic);
+__device__ __forceinline__ int seg_col(const Rows& A, int t, bool mir, int s, int c) {
+  if (MODE == 1) return rot_pixel(c, t, A.rot.ms, A.magic, mir);
   if (MODE == 2) return c + s * A.rot.q * A.rot.n_ell;
   return c;
 }
@@ -177,7 +189,7 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
                                                   int64_t bsx, float* __restrict__ y, int64_t ldy,
                                                   int64_t bsy, int ncols, int G, int R, int TG,
                                                   int S, int ms, int n_ell, int q,
-                                                  uint64_t magic) {
+                                                  int mirror, uint64_t magic) {
   const int lane = threadIdx.x & 31;
   const int lr = block_row(G, R, TG, S);
   if (lr < 0 || lr >= rows) return;
@@ -189,10 +201,16 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
 #pragma unroll
   for (int k = 0; k < CH; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
   int t = 0, sr = row;
+  bool mir = false;
   if (MODE == 1) {
     const int j = row / n_ell, l = row - j * n_ell;
     t = j / q;
-    sr = (j - t * q) * n_ell + l;
+    int js = j - t * q;
+    if (mirror && 2 * js > q) {  // 8-fold form: stored column q - js, mirrored
+      js = q - js;
+      mir = true;
+    }
+    sr = js * n_ell + l;
   }
 #pragma unroll 1
   for (int s = 0; s < (MODE == 2 ? 4 : 1); ++s) {
@@ -204,7 +222,7 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
       float v = 0.f;
       if (eb + lane < e1) {
         c = col[eb + lane];
-        c = MODE == 1 ? rot_pixel(c, t, ms, magic) : c + off;
+        c = MODE == 1 ? rot_pixel(c, t, ms, magic, mir) : c + off;
         v = wval<V>(val[eb + lane]);
       }
       const int cnt = min(32, e1 - eb);
@@ -255,6 +273,7 @@ __global__ void __launch_bounds__(256) k_spmm_scalar(Rows A, const int32_t* __re
   for (int q = 0; q < PER; ++q) acc[q] = 0.f;
   constexpr int NSEG = MODE == 2 ? 4 : 1;
   const int t = MODE == 1 ? (row / A.rot.n_ell) / A.rot.q : 0;
+  const bool mir = MODE == 1 && seg_mirrored(A, row / A.rot.n_ell);
   for (int s = 0; s < NSEG; ++s) {
     const int sr = seg_row<MODE>(A, row, s);
     const int e0 = rowptr[sr], e1 = rowptr[sr + 1];
@@ -262,7 +281,7 @@ __global__ void __launch_bounds__(256) k_spmm_scalar(Rows A, const int32_t* __re
       int c = 0;
       float v = 0.f;
       if (eb + lane < e1) {
-        c = seg_col<MODE>(A, t, s, col[eb + lane]);
+        c = seg_col<MODE>(A, t, mir, s, col[eb + lane]);
         v = wval<V>(val[eb + lane]);
       }
       const int cnt = min(32, e1 - eb);
@@ -314,7 +333,7 @@ int launch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t
 #define SRT_ROT_LAUNCH(C)                                                                     \
   k_spmm_rot<V, C, MODE><<<grid, block, 0, st>>>(W.rows, W.r0, A.rowptr, A.col, val, x, ldx, \
                                                  bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG,    \
-                                                 W.S, r.ms, r.n_ell, r.q, W.magic)
+                                                 W.S, r.ms, r.n_ell, r.q, r.mirror, W.magic)
     switch (CH) {
       case 4: SRT_ROT_LAUNCH(4); break;
       case 3: SRT_ROT_LAUNCH(3); break;

@@ -297,7 +297,7 @@ int srt_build_taps(srt_plan_s* plan, const SrtCsr& T, int64_t* nnz2, int64_t* by
     }
   SRT_TRY(upload(fp, fk, f32, f16, &plan->tf, bytes));
   SRT_TRY(upload(ap, ak, a32, a16, &plan->ta, bytes));
-  if (!(plan->g.flags & SRT_TAPS_ROWWISE)) {
+  if (!(plan->g.flags & SRT_ROWWISE)) {
     SRT_TRY(srt_build_tiles(plan, rp, col, v32, v16, bytes));
     plan->tiles = 1;
   }

@@ -579,16 +579,20 @@ def main(argv=None):
     out["budget_gb_per_server"] = budget / 2**30
     for rate in rates:
         acc = {n: dict(reqs=[], wall=0.0, batches=0, hist=collections.Counter(), failed=0,
-                       evictions=0) for n in names}
+                       evictions=0, seg=[]) for n in names}
         for seg in range(a.segments):
             for name in (names if seg % 2 == 0 else names[::-1]):
                 srv, ac = servers[name], acc[name]
                 base = dict(srv.stats.__dict__)
                 base_hist = collections.Counter(srv.stats.batch_hist)
                 t0 = time.perf_counter()
-                ac["reqs"] += poisson_run(srv, rate, a.duration / a.segments, payloads,
-                                          seed=3 + 1000 * seg, drop_results=True,
-                                          max_requests=max(1, a.max_requests // a.segments))
+                got = poisson_run(srv, rate, a.duration / a.segments, payloads,
+                                  seed=3 + 1000 * seg, drop_results=True,
+                                  max_requests=max(1, a.max_requests // a.segments))
+                ac["reqs"] += got
+                sl = latency_summary([r for r in got if r.error is None and not r.cancelled])
+                if sl["n"]:
+                    ac["seg"].append((round(sl["p50_ms"], 3), round(sl["p99_ms"], 3)))
                 ac["wall"] += time.perf_counter() - t0
                 ac["batches"] += srv.stats.batches - base["batches"]
                 ac["hist"] += srv.stats.batch_hist - base_hist
@@ -604,7 +608,10 @@ def main(argv=None):
                 failed=ac["failed"], batches=ac["batches"],
                 mean_batch=len(ok) / max(1, ac["batches"]),
                 batch_hist={int(k): int(v) for k, v in sorted(ac["hist"].items())},
-                evictions=ac["evictions"], hbm_used_gb=srv.used_bytes() / 2**30))
+                evictions=ac["evictions"], hbm_used_gb=srv.used_bytes() / 2**30,
+                # the same arrivals segment by segment: the spread of p50 / p99
+                # over segments is the run-to-run noise a mode difference must beat
+                segment_p50_p99_ms=ac["seg"]))
             print(json.dumps(out["runs"][-1]), flush=True)
     for srv in servers.values():
         srv.close()

@@ -41,15 +41,16 @@ class Geometry:
     csr_only: bool = False
     a1_rotation: bool = False
     rho_linear: bool = False  # intermediate piecewise linear in rho (else constant on bins)
-    taps_rowwise: bool = False  # A2 from the taps a warp per row (else 2 x 2 row tiles)
+    rowwise: bool = False  # every product a warp per output row (else register tiles of rows)
     n_phi_total: int = 0  # > 0: the plan holds columns phi_first .. + n_phi - 1 of this many
     phi_first: int = 0
+    a1_full: bool = False  # store A1 for every column (else for the aperture's symmetry set)
 
     @staticmethod
     def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, **options) -> "Geometry":
         """Default readings, computed by the library (srt_geometry_default);
         options set weight_dtype / keep_f64 / csr_only / a1_rotation / rho_linear /
-        taps_rowwise."""
+        rowwise / a1_full."""
         g = L.SrtGeometry()
         check(L.lib().srt_geometry_default(ctypes.byref(g), ms, mz, dxy, dz, radius, n_phi, n_zs,
                                            n_ell), "srt_geometry_default")
@@ -79,7 +80,8 @@ class Geometry:
                              | (L.SRT_CSR_ONLY if self.csr_only else 0)
                              | (L.SRT_A1_ROTATION if self.a1_rotation else 0)
                              | (L.SRT_RHO_LINEAR if self.rho_linear else 0)
-                             | (L.SRT_TAPS_ROWWISE if self.taps_rowwise else 0),
+                             | (L.SRT_ROWWISE if self.rowwise else 0)
+                             | (L.SRT_A1_FULL if self.a1_full else 0),
                              self.n_phi_total, self.phi_first)
 
     @property

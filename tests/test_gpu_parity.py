@@ -308,7 +308,7 @@ def test_toeplitz_second_stage(srt, orc, sz, wdt):
     b = srt.Plan(g.with_(csr_only=True))
     assert a.info["a2_taps"] == 1 and a.info["n_taps"] > 0 and b.info["a2_taps"] == 0
     assert a.info["nnz2"] == b.info["nnz2"]
-    assert srt.Plan(g.with_(taps_rowwise=True)).info["device_bytes"] < b.info["device_bytes"]
+    assert srt.Plan(g.with_(rowwise=True)).info["device_bytes"] < b.info["device_bytes"]
     for which in (2, 4):
         ra, ca, va, _ = a.export(which)
         rb, cb, vb, _ = b.export(which)
@@ -400,24 +400,41 @@ def test_plan_info_and_timing(srt, orc):
 
 ROT = [dict(I.sizes("srt32")),
        dict(ms=7, mz=5, dxy=0.5, dz=0.37, radius=6.0, n_phi=8, n_zs=3, n_ell=13, phi0=0.2),
-       dict(ms=12, mz=9, dxy=0.4, dz=0.3, radius=6.0, n_phi=12, n_zs=5, n_ell=21, zs=(-1.0, 1.2))]
+       dict(ms=12, mz=9, dxy=0.4, dz=0.3, radius=6.0, n_phi=12, n_zs=5, n_ell=21, zs=(-1.0, 1.2)),
+       dict(ms=10, mz=8, dxy=0.5, dz=0.5, radius=6.0, n_phi=16, n_zs=8, n_ell=13,
+            zs=(-2.0 + 0.15, 2.0 + 0.15)),                 # 8-fold, odd radius count
+       dict(ms=6, mz=4, dxy=0.5, dz=0.5, radius=4.0, n_phi=8, n_zs=4, n_ell=9)]  # q = 2
+
+
+def _sym_form(sz, **form):
+    """The symmetry form the plan should choose (srt.h, SRT_A1_FULL)."""
+    if form.get("a1_full") or sz["n_phi"] % 4:
+        return 0
+    tiles = sz["ms"] % 2 == 0 and sz["mz"] % 4 == 0 and not form.get("rowwise")
+    eight = tiles and sz["n_phi"] % 8 == 0 and sz.get("phi0", 0.0) == 0.0
+    return 2 if eight and not form.get("a1_rotation") else 1
 
 
 @pytest.mark.parametrize("sz", ROT)
+@pytest.mark.parametrize("form", [{}, dict(a1_rotation=True), dict(rowwise=True)])
 @pytest.mark.parametrize("wdt", ["fp32", "bf16"])
-def test_a1_by_rotation(srt, orc, sz, wdt):
-    """With SRT_A1_ROTATION and n_phi a multiple of 4 the plan stores A1 for
-    the first n_phi/4 sensor columns only; column j + n_phi/4 sees the pixel
-    grid turned by 90 degrees.  The full A1 and A1^T it stands for (exported) have the pattern
-    of the directly assembled ones and their FP64 entries to rounding, and the
-    transforms match the fully stored plan and the oracle (odd ms, a phase
-    phi0, rings off the slab centres, BF16, batch 2)."""
+def test_a1_by_symmetry(srt, orc, sz, form, wdt):
+    """By default the plan stores A1 for a fundamental set of sensor columns:
+    the first n_phi/8 + 1 under quarter turns and the diagonal mirror (the
+    8-fold form; n_phi % 8 == 0, phi0 = 0, ms even, mz % 4 == 0), else the
+    first n_phi/4 under quarter turns.  The full A1 and A1^T it stands for
+    (exported) have the pattern of the directly assembled ones and their FP64
+    entries to rounding, and the transforms (tile and row-per-warp kernels)
+    match the fully stored plan and the oracle (odd ms, a phase phi0, rings
+    off the slab centres, an odd radius count, two stored columns that are
+    both fixed by a mirror, BF16, batch 2)."""
     g, o = geom_pair(orc, weight_dtype=wdt, keep_f64=True, **sz)
-    a = srt.Plan(g.with_(a1_rotation=True))
-    b = srt.Plan(g)
-    assert a.info["a1_rot"] == 1 and b.info["a1_rot"] == 0
+    a = srt.Plan(g.with_(**form))
+    b = srt.Plan(g.with_(a1_full=True, rowwise=True))
+    assert a.info["a1_rot"] == _sym_form(sz, **form) and b.info["a1_rot"] == 0
     assert a.info["rows1"] == b.info["rows1"] and a.info["nnz1"] == b.info["nnz1"]
-    assert a.info["device_bytes"] < b.info["device_bytes"]
+    if a.info["a1_rot"]:
+        assert a.info["device_bytes"] < srt.Plan(g.with_(a1_full=True, **form)).info["device_bytes"]
     for which in (1, 3):
         ra, ca, va, da = a.export(which, f64=True)
         rb, cb, vb, db = b.export(which, f64=True)
@@ -436,6 +453,27 @@ def test_a1_by_rotation(srt, orc, sz, wdt):
     lhs, rhs = srt.dot_f64(a.forward(f), y), srt.dot_f64(f, a.adjoint(y))
     nrm = math.sqrt(srt.dot_f64(a.forward(f), a.forward(f)) * srt.dot_f64(y, y))
     assert abs(lhs - rhs) / nrm <= ADJ_TOL
+
+
+@pytest.mark.parametrize("sz", [dict(I.sizes("srt32")), ROT[3], ROT[4],
+                                dict(ms=14, mz=12, dxy=0.4, dz=0.4, radius=6.0, n_phi=6, n_zs=7,
+                                     n_ell=18, phi0=0.3)])
+@pytest.mark.parametrize("wdt", ["fp32", "bf16"])
+@pytest.mark.parametrize("batch", [1, 3])
+def test_a1_tiles_equal_rowwise(srt, orc, sz, wdt, batch):
+    """With A1 stored for every column, the 2 x 2 pixel A1^T tiles sum every
+    pixel's entries in the CSR order of A1^T (ascending (j, l)) and add only
+    zeros besides, and the A2 tiles those of the taps: forward and adjoint
+    equal the row-per-warp kernels bitwise (after +0.0, which equates the
+    signs of zero sums)."""
+    import torch
+    g, _ = geom_pair(orc, weight_dtype=wdt, a1_full=True, **sz)
+    a, b = srt.Plan(g), srt.Plan(g.with_(rowwise=True))
+    rng = np.random.default_rng(33)
+    f = to_dev(rng.uniform(0, 1, (batch, *g.f_shape)))
+    y = to_dev(rng.standard_normal((batch, *g.p_shape)))
+    assert torch.equal(a.forward(f) + 0.0, b.forward(f) + 0.0)
+    assert torch.equal(a.adjoint(y) + 0.0, b.adjoint(y) + 0.0)
 
 
 def test_concurrent_calls_on_one_plan(srt, orc):
@@ -502,11 +540,13 @@ TILE_GEOMS = [dict(I.sizes("srt32")), dict(I.sizes("srt16fd")),
 def test_tiles_equal_rowwise_taps(srt, orc, sz, wdt, batch):
     """The 2 x 2 row tiles sum every row in the order of the row-per-warp
     taps kernel and add only zeros besides, so forward and adjoint agree
-    bitwise (after +0.0, which equates the signs of zero sums); odd ring,
-    slab and radius counts leave half-empty tiles at the edges."""
+    bitwise (after +0.0, which equates the signs of zero sums; A1 stored for
+    every column in both plans, where its tiles are bitwise the CSR rows
+    too); odd ring, slab and radius counts leave half-empty tiles at the
+    edges."""
     import torch
-    g, o = geom_pair(orc, weight_dtype=wdt, **sz)
-    gr, _ = geom_pair(orc, weight_dtype=wdt, taps_rowwise=True, **sz)
+    g, o = geom_pair(orc, weight_dtype=wdt, a1_full=True, **sz)
+    gr, _ = geom_pair(orc, weight_dtype=wdt, a1_full=True, rowwise=True, **sz)
     plan, ref = srt.Plan(g), srt.Plan(gr)
     assert plan.info["a2_taps"] == 1
     rng = np.random.default_rng(31)

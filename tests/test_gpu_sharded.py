@@ -30,7 +30,9 @@ def srt():
 def test_column_blocks_compose_the_whole_transform(srt, orc, sz, cuts, wdt):
     import torch
     g, o = geom_pair(orc, weight_dtype=wdt, **sz)
-    whole = srt.Plan(g)
+    # a block stores A1 for each of its columns; so does the whole plan here
+    # (by default it would keep a symmetric subset and derive the rest)
+    whole = srt.Plan(g.with_(a1_full=True))
     rng = np.random.default_rng(41)
     f = to_dev(rng.uniform(0, 1, (2, *g.f_shape)))
     y = to_dev(rng.standard_normal((2, *g.p_shape)))
