@@ -138,6 +138,9 @@ typedef struct srt_plan_info_t {
                               /* 2: the first n_phi/8 + 1, by quarter turns   */
                               /*    and the diagonal mirror; 0: every column  */
   int32_t reserved;
+  int64_t tile_records[3];    /* records of the register-tile products: A2,   */
+                              /* A2^T (2 x 2 row tiles) and A1^T (2 x 2 pixel */
+                              /* tiles); 0 where that product runs row-wise   */
 } srt_plan_info_t;
 
 /*
@@ -286,6 +289,25 @@ int srt_forward_noalloc(srt_plan_t plan, const float* f, float* p, int32_t batch
 /* The matched adjoint (as srt_adjoint) on the same scratch, with the same
  * limits, errors and ordering rule. */
 int srt_adjoint_noalloc(srt_plan_t plan, const float* p, float* f, int32_t batch, void* stream);
+
+/*
+ * Debug builds (the library compiled with -DSRT_CHECKS; the package's
+ * build.build_checked() makes one): every product kernel checks each
+ * gathered row index against the row count of the operand it reads, before
+ * the access.  An index outside the operand is counted and replaced by row 0,
+ * so it is reported without a fault; srt_forward / srt_adjoint and the
+ * host-buffer calls (and the no-alloc calls, which run them) then
+ * synchronise their stream and return SRT_ERR_CUDA if a check failed during
+ * the call (pipelined calls are reported by srt_checks_read only).
+ *   srt_checks_read: *violations = indices found outside their operand since
+ *     the last read (synchronises the device), then resets the count.
+ *   srt_checks_cap: count every operand as having at most `rows` rows (0: no
+ *     cap), so that a test can make in-range indices trip the check without
+ *     any access outside an operand.
+ * Release builds compile the checks away; both calls return SRT_ERR_ARG there.
+ */
+int srt_checks_read(int64_t* violations);
+int srt_checks_cap(int32_t rows);
 
 /*
  * FP64 inner product on the device: *out = sum_i (double)a[i] * (double)b[i],

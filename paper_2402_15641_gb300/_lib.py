@@ -43,6 +43,7 @@ class SrtPlanInfo(ctypes.Structure):
         ("device_bytes", ctypes.c_int64), ("weight_dtype", ctypes.c_int32),
         ("a2_taps", ctypes.c_int32), ("n_taps", ctypes.c_int64),
         ("a1_rot", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("tile_records", ctypes.c_int64 * 3),
     ]
 
 
@@ -76,6 +77,8 @@ SIGNATURES = {
     "srt_pipe_destroy": (ctypes.c_int, [_VP]),
     "srt_plan_destroy": (ctypes.c_int, [_VP]),
     "srt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "srt_checks_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64)]),
+    "srt_checks_cap": (ctypes.c_int, [_I32]),
 }
 
 
@@ -89,20 +92,25 @@ class SrtError(RuntimeError):
 _lib = None
 
 
+def load(path: str):
+    """A libsrt build at `path` with every ABI signature declared."""
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{os.path.basename(path)} not found at {path}: build it with "
+            "`python -m paper_2402_15641_gb300.build` (there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
 def lib():
     """Load libsrt.so once; raises if it has not been built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(
-                f"libsrt.so not found at {LIB_PATH}: build it with "
-                "`python -m paper_2402_15641_gb300.build` (there is no CPU fallback)")
-        L = ctypes.CDLL(LIB_PATH)
-        for name, (res, args) in SIGNATURES.items():
-            fn = getattr(L, name)
-            fn.restype = res
-            fn.argtypes = args
-        _lib = L
+        _lib = load(LIB_PATH)
     return _lib
 
 

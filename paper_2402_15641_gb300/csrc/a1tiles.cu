@@ -41,6 +41,10 @@
 
 namespace {
 
+#ifdef SRT_CHECKS
+__device__ unsigned long long g_viol;  // gathered rows outside their operand
+#endif
+
 // Records gathered per step of the main loops (as in tiles.cu).
 constexpr int kU = 6;
 
@@ -92,6 +96,7 @@ struct A1Args {
   int mode, q, ms, n_phi, n_ell, ntx;
   int G, R, TG, S;     // block order
   int g0, g1;          // tile rows [g0, g1) (pixel rows 2 g0 .. 2 g1 - 1)
+  int xrows;           // rows of the gathered operand (debug-build checks)
 };
 
 // Warp -> (group, index) as in spmm.cu's block_row: G groups of R, a block
@@ -142,7 +147,9 @@ __device__ __forceinline__ void a1t_pass(const A1Args& A, const W* __restrict__ 
     const int j = k >> 16, l = k & 0xffff;
     int J = PM ? base - j : base + j;
     if (J >= A.n_phi) J -= A.n_phi;
-    return J * A.n_ell + l;
+    int row = J * A.n_ell + l;
+    SRT_CHECK_GATHER(0, row, A.xrows, g_viol);
+    return row;
   };
   int e = e0;
 #pragma unroll 1
@@ -376,6 +383,7 @@ int srt_a1tiles_apply(const srt_plan_s* plan, int g0, int g1, const float* x, in
   A.n_phi = g.n_phi;
   A.n_ell = g.n_ell;
   A.ntx = t.ntx;
+  A.xrows = srt_checked_rows((int64_t)g.n_phi * g.n_ell);
   // tiles (ta, tb), ta in [g0, g1): blocks of 4 x 2 tiles (8 x 4 pixels)
   // walked in 16 x 16 tile (32 x 32 pixel) super-tiles where they fit, so
   // the rows gathered at any time belong to a compact patch (1.457 ms at
@@ -394,4 +402,15 @@ int srt_a1tiles_apply(const srt_plan_s* plan, int g0, int g1, const float* x, in
   const float4* w = reinterpret_cast<const float4*>(t.aw32);
   if (!w) return SRT_ERR_ARG;
   return launch_a1t<float4>(A, w, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
+}
+
+long long srt_checks_take_a1tiles() {
+#ifdef SRT_CHECKS
+  unsigned long long v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_viol, sizeof(v)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(g_viol, &z, sizeof(z)) != cudaSuccess) return -1;
+  return (long long)v;
+#else
+  return 0;
+#endif
 }

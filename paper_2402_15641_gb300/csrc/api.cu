@@ -303,6 +303,36 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
   return SRT_OK;
 }
 
+// Debug builds (-DSRT_CHECKS): bad gathered rows counted by the kernels and
+// not yet reported by srt_checks_read, and the test cap on operand rows.
+long long g_checks_total = 0;
+int g_checks_cap = 0;
+
+long long checks_take_all() {
+  long long n = 0;
+  for (long long v : {srt_checks_take_spmm(), srt_checks_take_taps(), srt_checks_take_tiles(),
+                      srt_checks_take_a1tiles()}) {
+    if (v < 0) return -1;
+    n += v;
+  }
+  return n;
+}
+
+// After a call in a debug build: wait for it and report a failed check.
+int checks_after(int status, cudaStream_t st) {
+#ifdef SRT_CHECKS
+  if (status != SRT_OK) return status;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SRT_ERR_CUDA;
+  const long long n = checks_take_all();
+  if (n < 0) return SRT_ERR_CUDA;
+  g_checks_total += n;
+  return n ? SRT_ERR_CUDA : SRT_OK;
+#else
+  (void)st;
+  return status;
+#endif
+}
+
 // The plan's matrices live on the device it was built on: a call made with
 // another device current would launch there with pointers into the plan's
 // device memory, so it is refused before any work.
@@ -319,6 +349,8 @@ int common_checks(srt_plan_t plan, const void* a, const void* b, int32_t batch) 
 }
 
 }  // namespace
+
+int srt_checks_rowcap() { return g_checks_cap; }
 
 extern "C" {
 
@@ -390,6 +422,9 @@ int srt_plan_info(srt_plan_t p, srt_plan_info_t* o) {
   o->n_taps = p->toeplitz ? p->tm.nnz : 0;
   o->a1_rot = p->a1_rot;
   o->reserved = 0;
+  o->tile_records[0] = p->tiles ? p->tlf.nrec : 0;
+  o->tile_records[1] = p->tiles ? p->tla.nrec : 0;
+  o->tile_records[2] = p->a1tiles ? p->a1tl.na : 0;
   return SRT_OK;
 }
 
@@ -405,7 +440,7 @@ int srt_forward(srt_plan_t p, const float* f, float* out, int32_t batch, void* w
   SRT_TRY(check_ws(p, batch, ws, ws_bytes));
   float* w0 = (float*)ws;
   float* w1 = w0 + align256(buf_elems(p->g, batch) * 4) / 4;
-  return run_forward(p, f, out, batch, w0, w1, S(stream));
+  return checks_after(run_forward(p, f, out, batch, w0, w1, S(stream)), S(stream));
 }
 
 int srt_adjoint(srt_plan_t p, const float* in, float* f, int32_t batch, void* ws,
@@ -414,7 +449,7 @@ int srt_adjoint(srt_plan_t p, const float* in, float* f, int32_t batch, void* ws
   SRT_TRY(check_ws(p, batch, ws, ws_bytes));
   float* w0 = (float*)ws;
   float* w1 = w0 + align256(buf_elems(p->g, batch) * 4) / 4;
-  return run_adjoint(p, in, f, batch, w0, w1, S(stream));
+  return checks_after(run_adjoint(p, in, f, batch, w0, w1, S(stream)), S(stream));
 }
 
 int srt_host_workspace_bytes(srt_plan_t p, int32_t batch, size_t* bytes) {
@@ -468,7 +503,7 @@ static int host_call(srt_plan_t p, int dir, const float* in_h, float* out_h, int
   if ((!ok_st || !ok_cs) && s == SRT_OK) s = SRT_ERR_CUDA;
   if (ok_cs) host_set_give(p, cp);
   else host_set_destroy(cp);
-  return s;
+  return checks_after(s, st);
 }
 
 int srt_forward_host(srt_plan_t p, const float* f_host, float* p_host, int32_t batch, void* ws,
@@ -843,6 +878,32 @@ int srt_launches_per_call(srt_plan_t p, int32_t dir, int32_t batch) {
 int srt_plan_destroy(srt_plan_t p) {
   free_plan(p);
   return SRT_OK;
+}
+
+int srt_checks_read(int64_t* violations) {
+#ifdef SRT_CHECKS
+  if (!violations) return SRT_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SRT_ERR_CUDA;
+  const long long n = checks_take_all();
+  if (n < 0) return SRT_ERR_CUDA;
+  *violations = g_checks_total + n;
+  g_checks_total = 0;
+  return SRT_OK;
+#else
+  (void)violations;
+  return SRT_ERR_ARG;
+#endif
+}
+
+int srt_checks_cap(int32_t rows) {
+#ifdef SRT_CHECKS
+  if (rows < 0) return SRT_ERR_ARG;
+  g_checks_cap = rows;
+  return SRT_OK;
+#else
+  (void)rows;
+  return SRT_ERR_ARG;
+#endif
 }
 
 const char* srt_error_string(int code) {

@@ -11,6 +11,41 @@
 
 #define SRT_PI 3.14159265358979323846264338327950288
 
+// Debug builds (-DSRT_CHECKS, build.py's checked library): every product
+// kernel checks each gathered row index base + off against its operand's row
+// count n before the access.  An index outside [0, n) is counted in the
+// translation unit's violation counter and replaced by row 0 (off = -base),
+// so a bad index is reported (srt_checks_read, and the call's status)
+// without touching memory outside the operand.  Release builds compile the
+// check away.
+#ifdef SRT_CHECKS
+#define SRT_CHECK_GATHER(base, off, n, counter)                                            \
+  do {                                                                                     \
+    if ((unsigned long long)((long long)(base) + (long long)(off)) >=                      \
+        (unsigned long long)(n)) {                                                         \
+      atomicAdd(&(counter), 1ull);                                                         \
+      (off) = -(base);                                                                     \
+    }                                                                                      \
+  } while (0)
+#else
+#define SRT_CHECK_GATHER(base, off, n, counter) \
+  do {                                          \
+  } while (0)
+#endif
+
+// Violations counted by each translation unit's kernels since the last
+// call, then reset (0 in release builds), and the row cap of srt_checks_cap.
+long long srt_checks_take_spmm();
+long long srt_checks_take_taps();
+long long srt_checks_take_tiles();
+long long srt_checks_take_a1tiles();
+int srt_checks_rowcap();
+// The operand row count a launch checks against: n, or the test cap if lower.
+inline int srt_checked_rows(int64_t n) {
+  const int cap = srt_checks_rowcap();
+  return (cap > 0 && cap < n) ? cap : (int)(n > 0x7fffffff ? 0x7fffffff : n);
+}
+
 // Return SRT_ERR_CUDA from the enclosing function when a runtime call fails.
 #define SRT_CUDA_TRY(expr)                         \
   do {                                             \

@@ -21,6 +21,9 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+#ifdef SRT_CHECKS
+__device__ unsigned long long g_viol;  // gathered rows outside their operand
+#endif
 
 template <typename V>
 __device__ __forceinline__ float wval(V v);
@@ -90,6 +93,7 @@ struct Rows {
   int S;           // super-tile side of the block order (0: chunk-major bands)
   SrtRot rot;
   uint64_t magic;  // ceil(2^40 / rot.ms)
+  int xrows;       // rows of the gathered operand (debug-build checks)
 };
 
 // Stored row and gathered-row remap of segment s of output row `row`.
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__(256) k_spmm_plain(int rows, const int32_t* __r
                                                     const float* __restrict__ x, int64_t ldx,
                                                     int64_t bsx, float* __restrict__ y,
                                                     int64_t ldy, int64_t bsy, int ncols, int G,
-                                                    int R, int TG, int S) {
+                                                    int R, int TG, int S, int xrows) {
   const int lane = threadIdx.x & 31;
   const int row = block_row(G, R, TG, S);
   if (row < 0 || row >= rows) return;
@@ -142,6 +146,7 @@ __global__ void __launch_bounds__(256) k_spmm_plain(int rows, const int32_t* __r
     float v = 0.f;
     if (eb + lane < e1) {
       c = col[eb + lane];
+      SRT_CHECK_GATHER(0, c, xrows, g_viol);
       v = wval<V>(val[eb + lane]);
     }
     const int cnt = min(32, e1 - eb);
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
                                                   int64_t bsx, float* __restrict__ y, int64_t ldy,
                                                   int64_t bsy, int ncols, int G, int R, int TG,
                                                   int S, int ms, int n_ell, int q,
-                                                  int mirror, uint64_t magic) {
+                                                  int mirror, uint64_t magic, int xrows) {
   const int lane = threadIdx.x & 31;
   const int lr = block_row(G, R, TG, S);
   if (lr < 0 || lr >= rows) return;
@@ -223,6 +228,7 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
       if (eb + lane < e1) {
         c = col[eb + lane];
         c = MODE == 1 ? rot_pixel(c, t, ms, magic, mir) : c + off;
+        SRT_CHECK_GATHER(0, c, xrows, g_viol);
         v = wval<V>(val[eb + lane]);
       }
       const int cnt = min(32, e1 - eb);
@@ -282,6 +288,7 @@ __global__ void __launch_bounds__(256) k_spmm_scalar(Rows A, const int32_t* __re
       float v = 0.f;
       if (eb + lane < e1) {
         c = seg_col<MODE>(A, t, mir, s, col[eb + lane]);
+        SRT_CHECK_GATHER(0, c, A.xrows, g_viol);
         v = wval<V>(val[eb + lane]);
       }
       const int cnt = min(32, e1 - eb);
@@ -320,10 +327,10 @@ int launch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t
     const int CH = chunks >= 4 ? 4 : chunks;
     dim3 grid(gx, CH == 4 ? (ncols + 511) / 512 : 1, batch);
     switch (CH) {
-      case 4: k_spmm_plain<V, 4><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S); break;
-      case 3: k_spmm_plain<V, 3><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S); break;
-      case 2: k_spmm_plain<V, 2><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S); break;
-      default: k_spmm_plain<V, 1><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S); break;
+      case 4: k_spmm_plain<V, 4><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S, W.xrows); break;
+      case 3: k_spmm_plain<V, 3><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S, W.xrows); break;
+      case 2: k_spmm_plain<V, 2><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S, W.xrows); break;
+      default: k_spmm_plain<V, 1><<<grid, block, 0, st>>>(W.rows, rp, A.col, val, x, ldx, bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG, W.S, W.xrows); break;
     }
   } else if (vec) {
     const int chunks = (ncols + 127) / 128;
@@ -333,7 +340,8 @@ int launch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t
 #define SRT_ROT_LAUNCH(C)                                                                     \
   k_spmm_rot<V, C, MODE><<<grid, block, 0, st>>>(W.rows, W.r0, A.rowptr, A.col, val, x, ldx, \
                                                  bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG,    \
-                                                 W.S, r.ms, r.n_ell, r.q, r.mirror, W.magic)
+                                                 W.S, r.ms, r.n_ell, r.q, r.mirror, W.magic, \
+                                                 W.xrows)
     switch (CH) {
       case 4: SRT_ROT_LAUNCH(4); break;
       case 3: SRT_ROT_LAUNCH(3); break;
@@ -379,7 +387,21 @@ int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx,
   if (G > 0 && (int64_t)G * R != rows) G = 0;
   if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 1;
   if (G <= 0 || S <= 0 || G % S || R % S || S % TG || S % (8 / TG)) S = 0;
-  const Rows W{(int)rows, (int)r0, G, R, TG, S, rot, magic};
+  // gathered operand: A's columns, or for A1^T from the stored quarter
+  // (mode 2) the rows (j, l) of every sensor column
+  const int64_t xr = rot.mode == 2 ? (int64_t)4 * rot.q * rot.n_ell : A.cols;
+  const Rows W{(int)rows, (int)r0, G, R, TG, S, rot, magic, srt_checked_rows(xr)};
   if (wdt == SRT_BF16) return dispatch<uint16_t>(A, A.v16, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
   return dispatch<float>(A, A.v32, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
+}
+
+long long srt_checks_take_spmm() {
+#ifdef SRT_CHECKS
+  unsigned long long v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_viol, sizeof(v)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(g_viol, &z, sizeof(z)) != cudaSuccess) return -1;
+  return (long long)v;
+#else
+  return 0;
+#endif
 }

@@ -41,6 +41,10 @@
 
 namespace {
 
+#ifdef SRT_CHECKS
+__device__ unsigned long long g_viol;  // gathered rows outside their operand
+#endif
+
 struct TileArgs {
   const int32_t* ptr;  // [pairs][nkeys + 1]: first record of each key
   const int32_t* off;  // [records]: gathered-row offset
@@ -49,6 +53,7 @@ struct TileArgs {
   int c0, c1;          // tile coordinate range (forward: rings, adjoint: slabs)
   int n_ell, mz;
   int G, R, TG;        // block order: G coordinate pairs x R radius pairs
+  int xrows;           // rows of the gathered operand (debug-build checks)
 };
 
 template <typename W>
@@ -129,7 +134,10 @@ __global__ void __launch_bounds__(256) k_tile22(TileArgs A, const W* __restrict_
     float wu[U][4];
     float4 v[U][CH];
 #pragma unroll
-    for (int u = 0; u < U; ++u) o[u] = __ldg(A.off + e + u);
+    for (int u = 0; u < U; ++u) {
+      o[u] = __ldg(A.off + e + u);
+      SRT_CHECK_GATHER(xb, o[u], A.xrows, g_viol);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const float* xr = x0 + (int64_t)o[u] * ldx;
@@ -150,7 +158,8 @@ __global__ void __launch_bounds__(256) k_tile22(TileArgs A, const W* __restrict_
   }
 #pragma unroll 1
   for (; e < e1; ++e) {
-    const int o = __ldg(A.off + e);
+    int o = __ldg(A.off + e);
+    SRT_CHECK_GATHER(xb, o, A.xrows, g_viol);
     float w[4];
     tile_w<W>(wt + e, w);
     const float* xr = x0 + (int64_t)o * ldx;
@@ -304,7 +313,8 @@ int srt_tiles_apply(const srt_plan_s* plan, bool adjoint, int c0, int c1, int TG
     return SRT_ERR_ARG;
   if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 4;
   TileArgs A{t.ptr, t.off, t.nkeys, t.key0, adjoint ? g.n_zs : g.mz, c0, c1, g.n_ell, g.mz,
-             (c1 - c0 + 1) / 2, t.pairs, TG};
+             (c1 - c0 + 1) / 2, t.pairs, TG,
+             srt_checked_rows(adjoint ? (int64_t)g.n_zs * g.n_ell : (int64_t)g.n_ell * g.mz)};
   if (g.weight_dtype == SRT_BF16) {
     if (!t.w16) return SRT_ERR_ARG;
     const uint2* w = reinterpret_cast<const uint2*>(t.w16);
@@ -315,4 +325,15 @@ int srt_tiles_apply(const srt_plan_s* plan, bool adjoint, int c0, int c1, int TG
   const float4* w = reinterpret_cast<const float4*>(t.w32);
   return adjoint ? launch<float4, true>(A, w, x, (int)ldx, y, ldy, ncols, st)
                  : launch<float4, false>(A, w, x, (int)ldx, y, ldy, ncols, st);
+}
+
+long long srt_checks_take_tiles() {
+#ifdef SRT_CHECKS
+  unsigned long long v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_viol, sizeof(v)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(g_viol, &z, sizeof(z)) != cudaSuccess) return -1;
+  return (long long)v;
+#else
+  return 0;
+#endif
 }

@@ -37,6 +37,9 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+#ifdef SRT_CHECKS
+__device__ unsigned long long g_viol;  // gathered rows outside their operand
+#endif
 
 template <typename V>
 __device__ __forceinline__ float tap_w(V v);
@@ -54,6 +57,7 @@ struct TapArgs {
   const int32_t* key;     // packed (index, offset) per tap
   int mz, n_zs, n_ell, r0;  // r0: first output row of this launch
   int rows, G, R, TG;     // rows of this launch; block order (G groups of R, TG per block)
+  int xrows;              // rows of the gathered operand (debug-build checks)
 };
 
 // Block-to-row order as in spmm.cu: with G > 0 a block owns TG groups x 8/TG
@@ -105,6 +109,7 @@ __global__ void __launch_bounds__(256) k_taps(TapArgs A, const V* __restrict__ v
       // forward: off = q, gathered row l*mz + h + q - (nz-1)
       // adjoint: off = e, h = k + e - (mz-1), gathered row h*n_ell + m
       c = ADJ ? (b + off - (mz - 1)) * A.n_ell + lo : lo * mz + a + off - (nz - 1);
+      SRT_CHECK_GATHER(0, c, A.xrows, g_viol);
       v = tap_w<V>(val[eb + lane]);
     }
     const int cnt = min(32, e1 - eb);
@@ -163,6 +168,7 @@ __global__ void __launch_bounds__(256) k_taps_scalar(TapArgs A, const V* __restr
       const int kk = A.key[eb + lane];
       const int lo = kk & 0xffff, off = kk >> 16;
       c = ADJ ? (b + off - (mz - 1)) * A.n_ell + lo : lo * mz + a + off - (nz - 1);
+      SRT_CHECK_GATHER(0, c, A.xrows, g_viol);
       v = tap_w<V>(val[eb + lane]);
     }
     const int cnt = min(32, e1 - eb);
@@ -312,7 +318,8 @@ int srt_taps_apply(const srt_plan_s* plan, bool adjoint, int64_t r0, int64_t row
   if (!t.rowptr || rows <= 0 || ncols <= 0) return SRT_ERR_ARG;
   if (G > 0 && (int64_t)G * R != rows) G = 0;
   if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 1;
-  TapArgs A{t.rowptr, t.key, g.mz, g.n_zs, g.n_ell, (int)r0, (int)rows, G, R, TG};
+  TapArgs A{t.rowptr, t.key, g.mz, g.n_zs, g.n_ell, (int)r0, (int)rows, G, R, TG,
+            srt_checked_rows(adjoint ? (int64_t)g.n_zs * g.n_ell : (int64_t)g.n_ell * g.mz)};
   if (g.weight_dtype == SRT_BF16) {
     if (!t.w16) return SRT_ERR_ARG;
     return adjoint ? launch<uint16_t, true>(A, t.w16, x, ldx, y, ldy, ncols, st)
@@ -321,4 +328,15 @@ int srt_taps_apply(const srt_plan_s* plan, bool adjoint, int64_t r0, int64_t row
   if (!t.w32) return SRT_ERR_ARG;
   return adjoint ? launch<float, true>(A, t.w32, x, ldx, y, ldy, ncols, st)
                  : launch<float, false>(A, t.w32, x, ldx, y, ldy, ncols, st);
+}
+
+long long srt_checks_take_taps() {
+#ifdef SRT_CHECKS
+  unsigned long long v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_viol, sizeof(v)) != cudaSuccess) return -1;
+  if (cudaMemcpyToSymbol(g_viol, &z, sizeof(z)) != cudaSuccess) return -1;
+  return (long long)v;
+#else
+  return 0;
+#endif
 }

@@ -112,13 +112,15 @@ _CPU = torch.device("cpu")
 class Plan:
     """An assembled operator pair (A1, A2 and transposes) resident on one GPU."""
 
-    def __init__(self, geom: Geometry, device=None, stream=None):
+    def __init__(self, geom: Geometry, device=None, stream=None, lib=None):
+        """lib: a loaded libsrt (_lib.load), e.g. the debug build with its
+        gathered-row checks; default: the package's libsrt.so."""
         if not torch.cuda.is_available():
             raise RuntimeError("srt.Plan needs a CUDA device; there is no CPU path")
         self.geom = geom
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
-        self._lib = L.lib()
+        self._lib = L.lib() if lib is None else lib
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(self._lib.srt_plan(ctypes.byref(geom.to_c()), ctypes.c_void_p(_stream_ptr(stream)),
@@ -128,6 +130,7 @@ class Plan:
         info = L.SrtPlanInfo()
         check(self._lib.srt_plan_info(self._h, ctypes.byref(info)), "srt_plan_info")
         self.info = {k: getattr(info, k) for k, _ in L.SrtPlanInfo._fields_ if k != "reserved"}
+        self.info["tile_records"] = list(info.tile_records)
 
     # -------------------------------------------------------------- memory
     def workspace_bytes(self, batch: int = 1) -> int:
