@@ -189,8 +189,12 @@ def stage_model(geom, info, batch, weights):
     # useful FMAs per gathered dense operand: 1 for a row-per-warp product;
     # entries per record for the register tiles (A1^T: stored entries, the
     # symmetry passes repeat entries and records alike)
+    # (A2: the records are per radius pair and key, each folding the taps of
+    # two rings or slabs, so entries per record = 2 n_taps / records away
+    # from the volume's ends)
     rec = info.get("tile_records") or [0, 0, 0]
-    for st, n_ent, r in ((spmm2, nnz2, rec[0]), (spmm2t, nnz2, rec[1]),
+    for st, n_ent, r in ((spmm2, 2 * info.get("n_taps", 0), rec[0]),
+                         (spmm2t, 2 * info.get("n_taps", 0), rec[1]),
                          (spmm1t, int(nnz1 * frac), rec[2])):
         st["fma_per_gather"] = round(n_ent / r, 3) if r else 1.0
     spmm1["fma_per_gather"] = 1.0
@@ -523,7 +527,8 @@ def run_ours(args):
                                                   "quarter turns and the diagonal mirror"}[
                                                       plan.info["a1_rot"]]
                                                   + ("; a warp per row" if args.rowwise
-                                                     else "; 4-radius and 2 x 2-pixel row tiles"),
+                                                     else "; A1 a warp per row, A1^T 2 x 2-pixel "
+                                                          "register tiles"),
                                       "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3),
                                       "intermediate": ("piecewise linear in rho" if args.rho_linear
                                                        else "piecewise constant on radius bins")}),
