@@ -46,6 +46,8 @@ def parse():
                    help="store A1 for a quarter of the sensor columns (quarter turns only, no mirror)")
     p.add_argument("--rowwise", action="store_true",
                    help="every product a warp per output row (else register tiles of rows)")
+    p.add_argument("--fuse-reshapes", action="store_true",
+                   help="P2 and P1^-1 folded into the A2 / A2^T tile products")
     p.add_argument("--a1-full", action="store_true",
                    help="store A1 for every sensor column (else for the aperture's symmetry set)")
     p.add_argument("--rho-linear", action="store_true",
@@ -162,8 +164,10 @@ def ncu_traffic(kernel_stage, workload):
     return float(v) if v else None
 
 
-def stage_model(geom, info, batch, weights):
-    """Algorithmic FLOPs and compulsory bytes per launch of each stage."""
+def stage_model(geom, info, batch, weights, fused=False):
+    """Algorithmic FLOPs and compulsory bytes per launch of each stage.
+    fused: A2 writes p and A2^T writes F1 in the reshaped layouts (no P2 and
+    P1^-1 kernels; their stages are dropped, the products' bytes unchanged)."""
     vb = 2 if weights == "bf16" else 4
     pix, c1 = geom.ms * geom.ms, geom.n_ell * geom.mz
     r1, r2 = geom.n_phi * geom.n_ell, geom.n_zs * geom.n_ell
@@ -200,6 +204,9 @@ def stage_model(geom, info, batch, weights):
     spmm1["fma_per_gather"] = 1.0
     p1 = dict(flop=0, bytes=2 * y1)
     p2 = dict(flop=0, bytes=2 * pp)
+    if fused:
+        return {"fwd": [("spmm1", spmm1), ("permute1", p1), ("spmm2", spmm2), None],
+                "adj": [("permute2_inv", p2), ("spmm2t", spmm2t), None, ("spmm1t", spmm1t)]}
     return {"fwd": [("spmm1", spmm1), ("permute1", p1), ("spmm2", spmm2), ("permute2", p2)],
             "adj": [("permute2_inv", p2), ("spmm2t", spmm2t), ("permute1_inv", p1),
                     ("spmm1t", spmm1t)]}
@@ -355,7 +362,8 @@ def run_ours(args):
     sz = I.sizes(args.workload)
     geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only,
                                a1_rotation=args.a1_rotation, rho_linear=args.rho_linear,
-                               rowwise=args.rowwise, a1_full=args.a1_full)
+                               rowwise=args.rowwise, a1_full=args.a1_full,
+                               fuse_reshapes=args.fuse_reshapes)
     B = args.batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -406,11 +414,15 @@ def run_ours(args):
     value = job_rate(world, args.steps, B, total_ms)
 
     # per-stage figures from the CUDA events recorded on the launch stream
-    model = stage_model(geom, plan.info, B, args.weights)
+    fused = plan.launches_per_call(0, B) == 3
+    model = stage_model(geom, plan.info, B, args.weights, fused)
     stages = {}
     for d in ("fwd", "adj"):
         mean = np.mean(np.array(stage[d]), axis=0)
-        for (name, m), ms in zip(model[d], mean):
+        for sm, ms in zip(model[d], mean):
+            if sm is None:  # a reshape fused into its product
+                continue
+            name, m = sm
             s = {"ms": round(float(ms), 5), "gb_s": round(m["bytes"] / (ms * 1e6), 1),
                  "hbm_frac": round(m["bytes"] / (ms * 1e6) / pk["hbm_gbs"], 4)}
             if m["flop"]:
@@ -529,6 +541,9 @@ def run_ours(args):
                                                   + ("; a warp per row" if args.rowwise
                                                      else "; A1 a warp per row, A1^T 2 x 2-pixel "
                                                           "register tiles"),
+                                      "reshapes": ("P2 and P1^-1 fused into the A2 / A2^T "
+                                                   "epilogues" if fused else
+                                                   "four reshape kernels"),
                                       "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3),
                                       "intermediate": ("piecewise linear in rho" if args.rho_linear
                                                        else "piecewise constant on radius bins")}),

@@ -77,6 +77,16 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  * n_phi/4 under quarter turns (n_phi % 4 == 0, the whole aperture), else
  * every column. */
 #define SRT_A1_FULL 0x40
+/* SRT_FUSE_RESHAPES: fold the reshapes P2 (forward) and P1^-1 (adjoint) into
+ * the products before them.  When A2 and A2^T are applied from register
+ * tiles (srt_plan_info_t.tile_records[0] > 0) and the dense width
+ * batch * n_phi is a multiple of 4, those products then write their output
+ * straight into the reshaped layout (p[b][j][h][m]; F1[b][j][l][k]) and a
+ * call makes 3 kernel launches instead of 4; the results are bitwise the
+ * same.  Off by default: the reshaped layouts take each dense column as a
+ * separate 16- or 32-byte piece, which costs the products more than the
+ * separate reshape kernels (which run at HBM speed) cost. */
+#define SRT_FUSE_RESHAPES 0x80
 /* When the rings are spaced like the slabs ((zs_hi - zs_lo) / n_zs = dz, any
  * n_zs, any offset; e.g. n_zs = mz over the volume height), ring h sits at
  * slab h + s plus a fixed fraction of a slab, A2[(h,m),(l,k)] = T[m, k-h-s, l]
@@ -340,6 +350,9 @@ int srt_plan_export(srt_plan_t plan, int32_t which, int32_t* rowptr, int32_t* co
  * then returns, for the LAST call in direction dir (0 forward, 1 adjoint), the
  * elapsed milliseconds of its stages in launch order (n >= 4: first SpMM,
  * permute, second SpMM, permute) after synchronising on the last event.
+ * With the fused reshapes (SRT_FUSE_RESHAPES) the fused permute's
+ * stage reads 0 and its time is part of the product before (forward) or
+ * after (adjoint) it.
  * Not for use with stream capture.  Errors: SRT_ERR_ARG, SRT_ERR_NOT_READY.
  */
 int srt_plan_set_timing(srt_plan_t plan, int32_t enable);

@@ -20,6 +20,7 @@ SRT_A1_ROTATION = 8
 SRT_RHO_LINEAR = 16
 SRT_ROWWISE = 32
 SRT_A1_FULL = 64
+SRT_FUSE_RESHAPES = 128
 SRT_NOALLOC_WORKSPACE_BYTES = 32 << 20
 
 

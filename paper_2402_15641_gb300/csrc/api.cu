@@ -189,6 +189,12 @@ int sink_copy(HostSink* hs, int chunk, cudaStream_t st, float* host, const float
 // Forward (Algorithm 1).  With a sink, the second product and the final
 // reshape run in kHostChunks ring ranges and each range of p is copied to
 // the host while the next one is computed (no per-stage timing then).
+// With SRT_FUSE_RESHAPES the tile products write their output in the layout
+// of the step after the reshape (P2 in the forward, P1^-1 in the adjoint).
+bool fused_reshapes(const srt_plan_s* p, int64_t nb) {
+  return p->tiles && nb % 4 == 0 && (p->g.flags & SRT_FUSE_RESHAPES);
+}
+
 int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, float* w1,
                 cudaStream_t st, HostSink* hs = nullptr) {
   const srt_geometry& g = p->g;
@@ -225,6 +231,12 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
     const int h0 = (int)((int64_t)g.n_zs * c / nc), h1 = (int)((int64_t)g.n_zs * (c + 1) / nc);
     const int64_t ra = (int64_t)h0 * g.n_ell, rn = (int64_t)(h1 - h0) * g.n_ell;
     NvRange r("A2 product + reshape P2");
+    if (fused_reshapes(p, nb)) {  // A2 tiles writing p[b][j][h][m] directly
+      SRT_TRY(srt_tiles_apply(p, false, h0, h1, 4, w1, nb, out, 0, (int)nb, st, r2));
+      if (!hs) mark(p, 0, 3, st);
+      if (hs) SRT_TRY(sink_copy(hs, c, st, hs->host + ra, out + ra, rn, r2, (int64_t)B * g.n_phi));
+      continue;
+    }
     if (p->tiles && nb % 4 == 0)  // A2 from 2 x 2 tiles of the master tensor's taps
       SRT_TRY(srt_tiles_apply(p, false, h0, h1, 4, w1, nb, w0 + ra * nb, nb, (int)nb, st));
     else if (p->toeplitz)  // A2 from the taps of the master tensor, a warp per row
@@ -261,9 +273,12 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
     SRT_TRY(srt_transpose(in, r2, (int64_t)g.n_phi * r2, w0, nb, g.n_phi, g.n_phi, (int)r2, B, st));
   }
   if (!hs) mark(p, 1, 1, st);
+  const bool fused = fused_reshapes(p, nb);
   {
-    NvRange r("A2^T product");
-    if (p->tiles && nb % 4 == 0)  // A2^T from 2 x 2 tiles of the master tensor's taps
+    NvRange r(fused ? "A2^T product + reshape P1^-1" : "A2^T product");
+    if (fused)  // A2^T tiles writing F1[b][j][l][k] directly
+      SRT_TRY(srt_tiles_apply(p, true, 0, g.mz, 4, w0, nb, w1, 0, (int)nb, st, c1));
+    else if (p->tiles && nb % 4 == 0)  // A2^T from 2 x 2 tiles of the master tensor's taps
       SRT_TRY(srt_tiles_apply(p, true, 0, g.mz, 4, w0, nb, w1, nb, (int)nb, st));
     else if (p->toeplitz)  // A2^T from the taps of the master tensor, a warp per row
       SRT_TRY(srt_taps_apply(p, true, 0, c1, 0, 0, 1, w0, nb, w1, nb, (int)nb, st));
@@ -271,11 +286,11 @@ int run_adjoint(srt_plan_s* p, const float* in, float* f, int B, float* w0, floa
       SRT_TRY(srt_spmm(p->a2t, g.weight_dtype, w0, nb, 0, w1, nb, 0, (int)nb, 1, st));
   }
   if (!hs) mark(p, 1, 2, st);
-  {
+  if (!fused) {
     NvRange r("reshape P1^-1");
     SRT_TRY(srt_transpose(w1, nb, g.n_phi, w0, c1, (int64_t)g.n_phi * c1, (int)c1, g.n_phi, B, st));
   }
-  const float* f1 = w0;  // F1[b][j][l][k], input of A1^T
+  const float* f1 = fused ? w1 : w0;  // F1[b][j][l][k], input of A1^T
   if (!hs) mark(p, 1, 3, st);
   // rows (pixels) in blocks of 4 x 2 pixels: a circle crossing a compact
   // tile touches more of its pixels than of a line of 8, so warps share L1;
@@ -870,9 +885,8 @@ int srt_stage_times(srt_plan_t p, int32_t dir, float* ms, int32_t n) {
 
 int srt_launches_per_call(srt_plan_t p, int32_t dir, int32_t batch) {
   (void)dir;
-  (void)batch;
-  if (!p) return 0;
-  return 4;
+  if (!p || batch <= 0) return 0;
+  return fused_reshapes(p, (int64_t)batch * p->g.n_phi) ? 3 : 4;
 }
 
 int srt_plan_destroy(srt_plan_t p) {

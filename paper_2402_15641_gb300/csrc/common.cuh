@@ -166,9 +166,13 @@ int srt_taps_apply(const srt_plan_s* plan, bool adjoint, int64_t r0, int64_t row
 
 // A2 (adjoint = false: ring rows [c0, c1), y at ring c0's first row) or A2^T
 // (adjoint = true: slabs [c0, c1) = [0, mz)) from the 2 x 2 tile records,
-// blocks of TG coordinate pairs x 8/TG radius pairs.
+// blocks of TG coordinate pairs x 8/TG radius pairs.  With ldn > 0 the
+// reshape that follows is fused (blocks of 4 x 2 pairs): the forward writes
+// y[n ldn + h n_ell + m] for every ring h in [c0, c1) (y at ring 0), the
+// adjoint y[n ldn + l mz + k]; ldy is then unused.
 int srt_tiles_apply(const srt_plan_s* plan, bool adjoint, int c0, int c1, int TG, const float* x,
-                    int64_t ldx, float* y, int64_t ldy, int ncols, cudaStream_t stream);
+                    int64_t ldx, float* y, int64_t ldy, int ncols, cudaStream_t stream,
+                    int64_t ldn = 0);
 
 // A1^T tile records from the plan's stored A1 (CSR on the device).
 int srt_build_a1tiles(srt_plan_s* plan, int64_t* bytes);

@@ -33,6 +33,14 @@
 // range.  Each output row therefore sums its entries in the order of the
 // taps kernel: ascending (offset, l) in the forward, ascending (h, m) (the
 // CSR order of A2^T) in the adjoint; the padded zero weights add +0.
+//
+// The reshape that follows each product in Algorithms 1 and 2 (P2 after A2,
+// P1^-1 after A2^T) can be folded into the product's epilogue (TR): the
+// block's 8 x 4 tile of output rows x its dense columns is staged in shared
+// memory and written in the layout the next step reads, column by column:
+//   forward: p[n][h][m] (n = b n_phi + j), 4 consecutive radii per store;
+//   adjoint: F1[n][l][k], 8 consecutive slabs per store (a 32-byte sector).
+// The sums are the same, so the two forms agree bitwise.
 #include <algorithm>
 #include <vector>
 
@@ -54,6 +62,7 @@ struct TileArgs {
   int n_ell, mz;
   int G, R, TG;        // block order: G coordinate pairs x R radius pairs
   int xrows;           // rows of the gathered operand (debug-build checks)
+  int64_t ldn;         // fused reshape: stride of the output's columns n
 };
 
 template <typename W>
@@ -105,19 +114,18 @@ __device__ __forceinline__ void fma4(float2 (&a)[2], float w, const float4& xv) 
 constexpr int kTileU = 6;
 
 // Lanes own 4 consecutive dense columns of each of CH 128-column chunks.
-template <typename W, bool ADJ, int CH>
+// TR: the block's outputs go through shared memory to the reshaped layout
+// (blocks of TG = 4 coordinate pairs x 2 radius pairs only).
+template <typename W, bool ADJ, int CH, bool TR>
 __global__ void __launch_bounds__(256) k_tile22(TileArgs A, const W* __restrict__ wt,
                                                 const float* __restrict__ x, int ldx,
                                                 float* __restrict__ y, int64_t ldy, int ncols) {
   const int lane = threadIdx.x & 31;
   int g, r;
-  if (!tile_of(A, &g, &r)) return;
+  const bool mine = tile_of(A, &g, &r);
+  if (!TR && !mine) return;  // (TR: every warp reaches the block barrier)
   const int c = A.c0 + 2 * g;
-  const int32_t* pp = A.ptr + (int64_t)r * (A.nkeys + 1) + (A.key0 - c);
-  const int e0 = pp[0], e1 = pp[A.E];
-  const int64_t xb = ADJ ? (int64_t)c * A.n_ell : (int64_t)c;
   const int n0 = blockIdx.y * (128 * CH) + lane * 4;
-  const float* x0 = x + xb * ldx + n0;
   bool in[CH];
 #pragma unroll
   for (int q = 0; q < CH; ++q) in[q] = n0 + q * 128 < ncols;
@@ -126,64 +134,126 @@ __global__ void __launch_bounds__(256) k_tile22(TileArgs A, const W* __restrict_
   for (int s = 0; s < 4; ++s)
 #pragma unroll
     for (int q = 0; q < CH; ++q) acc[s][q][0] = acc[s][q][1] = make_float2(0.f, 0.f);
-  constexpr int U = kTileU;
-  int e = e0;
+  if (mine) {
+    const int32_t* pp = A.ptr + (int64_t)r * (A.nkeys + 1) + (A.key0 - c);
+    const int e0 = pp[0], e1 = pp[A.E];
+    const int64_t xb = ADJ ? (int64_t)c * A.n_ell : (int64_t)c;
+    const float* x0 = x + xb * ldx + n0;
+    constexpr int U = kTileU;
+    int e = e0;
 #pragma unroll 1
-  for (; e + U <= e1; e += U) {
-    int o[U];
-    float wu[U][4];
-    float4 v[U][CH];
+    for (; e + U <= e1; e += U) {
+      int o[U];
+      float wu[U][4];
+      float4 v[U][CH];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      o[u] = __ldg(A.off + e + u);
-      SRT_CHECK_GATHER(xb, o[u], A.xrows, g_viol);
+      for (int u = 0; u < U; ++u) {
+        o[u] = __ldg(A.off + e + u);
+        SRT_CHECK_GATHER(xb, o[u], A.xrows, g_viol);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float* xr = x0 + (int64_t)o[u] * ldx;
+#pragma unroll
+        for (int q = 0; q < CH; ++q)
+          if (in[q]) v[u][q] = srt_ldg_keep(xr + q * 128);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) tile_w<W>(wt + e + u, wu[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < CH; ++q)
+          if (in[q]) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) fma4(acc[s][q], wu[u][s], v[u][q]);
+          }
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const float* xr = x0 + (int64_t)o[u] * ldx;
-#pragma unroll
-      for (int q = 0; q < CH; ++q)
-        if (in[q]) v[u][q] = srt_ldg_keep(xr + q * 128);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) tile_w<W>(wt + e + u, wu[u]);
-#pragma unroll
-    for (int u = 0; u < U; ++u)
+#pragma unroll 1
+    for (; e < e1; ++e) {
+      int o = __ldg(A.off + e);
+      SRT_CHECK_GATHER(xb, o, A.xrows, g_viol);
+      float w[4];
+      tile_w<W>(wt + e, w);
+      const float* xr = x0 + (int64_t)o * ldx;
 #pragma unroll
       for (int q = 0; q < CH; ++q)
         if (in[q]) {
+          const float4 xv = srt_ldg_keep(xr + q * 128);
 #pragma unroll
-          for (int s = 0; s < 4; ++s) fma4(acc[s][q], wu[u][s], v[u][q]);
+          for (int s = 0; s < 4; ++s) fma4(acc[s][q], w[s], xv);
         }
+    }
   }
-#pragma unroll 1
-  for (; e < e1; ++e) {
-    int o = __ldg(A.off + e);
-    SRT_CHECK_GATHER(xb, o, A.xrows, g_viol);
-    float w[4];
-    tile_w<W>(wt + e, w);
-    const float* xr = x0 + (int64_t)o * ldx;
+  if (!TR) {
 #pragma unroll
-    for (int q = 0; q < CH; ++q)
-      if (in[q]) {
-        const float4 xv = srt_ldg_keep(xr + q * 128);
+    for (int s = 0; s < 4; ++s) {
+      const int i = s >> 1, j = s & 1;
+      if (c + i >= A.c1 || 2 * r + j >= A.n_ell) continue;
+      const int64_t row = ADJ ? (int64_t)(2 * r + j) * A.mz + c + i
+                              : (int64_t)(c - A.c0 + i) * A.n_ell + 2 * r + j;
+      float* yr = y + row * ldy;
 #pragma unroll
-        for (int s = 0; s < 4; ++s) fma4(acc[s][q], w[s], xv);
+      for (int q = 0; q < CH; ++q) {
+        const int n = n0 + q * 128;
+        if (n < ncols)
+          *reinterpret_cast<float4*>(yr + n) =
+              make_float4(acc[s][q][0].x, acc[s][q][0].y, acc[s][q][1].x, acc[s][q][1].y);
       }
+    }
+    return;
   }
+  // fused reshape, 64 columns at a time (8 KB of shared memory, so that the
+  // L1 left for the gathers barely shrinks): S[cl][rl][n], cl = the block's
+  // coordinate 0..7 (ring or slab), rl = its radius 0..3 (radius or bin)
+  __shared__ __align__(16) float S[8 * 4 * 64];
+  const int w = threadIdx.x >> 5;
+  const int tiles = (A.G + 3) / 4;
+  const int ch = blockIdx.x / tiles, t = blockIdx.x - ch * tiles;
+  const int cb = A.c0 + 8 * t, rb = 4 * ch;  // the block's first coordinate and radius
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int i = s >> 1, j = s & 1;
-    if (c + i >= A.c1 || 2 * r + j >= A.n_ell) continue;
-    const int64_t row = ADJ ? (int64_t)(2 * r + j) * A.mz + c + i
-                            : (int64_t)(c - A.c0 + i) * A.n_ell + 2 * r + j;
-    float* yr = y + row * ldy;
+  for (int pass = 0; pass < 2 * CH; ++pass) {
+    const int q = pass >> 1, half = pass & 1;
+    if (pass) __syncthreads();  // the previous pass's reads are done
+    if ((lane >> 4) == half) {
 #pragma unroll
-    for (int q = 0; q < CH; ++q) {
-      const int n = n0 + q * 128;
-      if (n < ncols)
-        *reinterpret_cast<float4*>(yr + n) =
+      for (int s = 0; s < 4; ++s) {
+        const int cl = 2 * (w >> 1) + (s >> 1), rl = 2 * (w & 1) + (s & 1);
+        *reinterpret_cast<float4*>(S + (cl * 4 + rl) * 64 + (lane & 15) * 4) =
             make_float4(acc[s][q][0].x, acc[s][q][0].y, acc[s][q][1].x, acc[s][q][1].y);
+      }
+    }
+    __syncthreads();
+    const int nb0 = blockIdx.y * (128 * CH) + q * 128 + half * 64;
+    if (!ADJ) {
+      // p[n][h][m]: per (ring, column) the 4 radii rb .. rb + 3
+#pragma unroll
+      for (int it = threadIdx.x; it < 8 * 64; it += 256) {
+        const int cl = it >> 6, nl = it & 63, n = nb0 + nl, h = cb + cl;
+        if (h >= A.c1 || n >= ncols) continue;
+        const int64_t o = (int64_t)n * A.ldn + (int64_t)h * A.n_ell + rb;
+        const float* sp = S + cl * 4 * 64 + nl;
+        if (rb + 3 < A.n_ell && (o & 3) == 0) {
+          *reinterpret_cast<float4*>(y + o) = make_float4(sp[0], sp[64], sp[128], sp[192]);
+        } else {
+          for (int k = 0; k < 4 && rb + k < A.n_ell; ++k) y[o + k] = sp[k * 64];
+        }
+      }
+    } else {
+      // F1[n][l][k]: per (radius bin, column) the 8 slabs cb .. cb + 7
+      const int rl = threadIdx.x >> 6, nl = threadIdx.x & 63, n = nb0 + nl, l = rb + rl;
+      if (l < A.n_ell && n < ncols) {
+        const int64_t o = (int64_t)n * A.ldn + (int64_t)l * A.mz + cb;
+        const float* sp = S + rl * 64 + nl;
+        if (cb + 7 < A.c1 && (o & 3) == 0) {
+          *reinterpret_cast<float4*>(y + o) =
+              make_float4(sp[0], sp[256], sp[512], sp[768]);
+          *reinterpret_cast<float4*>(y + o + 4) =
+              make_float4(sp[1024], sp[1280], sp[1536], sp[1792]);
+        } else {
+          for (int k = 0; k < 8 && cb + k < A.c1; ++k) y[o + k] = sp[k * 256];
+        }
+      }
     }
   }
 }
@@ -196,10 +266,16 @@ int launch(const TileArgs& A, const W* w, const float* x, int ldx, float* y, int
   if (gx > 0x7fffffff) return SRT_ERR_ARG;
   const int CH = ncols > 128 ? 2 : 1;
   dim3 grid((unsigned)gx, (ncols + 128 * CH - 1) / (128 * CH), 1);
-  if (CH == 2)
-    k_tile22<W, ADJ, 2><<<grid, 256, 0, st>>>(A, w, x, ldx, y, ldy, ncols);
-  else
-    k_tile22<W, ADJ, 1><<<grid, 256, 0, st>>>(A, w, x, ldx, y, ldy, ncols);
+  if (A.ldn > 0) {
+    if (CH == 2)
+      k_tile22<W, ADJ, 2, true><<<grid, 256, 0, st>>>(A, w, x, ldx, y, ldy, ncols);
+    else
+      k_tile22<W, ADJ, 1, true><<<grid, 256, 0, st>>>(A, w, x, ldx, y, ldy, ncols);
+  } else if (CH == 2) {
+    k_tile22<W, ADJ, 2, false><<<grid, 256, 0, st>>>(A, w, x, ldx, y, ldy, ncols);
+  } else {
+    k_tile22<W, ADJ, 1, false><<<grid, 256, 0, st>>>(A, w, x, ldx, y, ldy, ncols);
+  }
   SRT_CUDA_TRY(cudaGetLastError());
   return SRT_OK;
 }
@@ -304,17 +380,19 @@ int srt_build_tiles(srt_plan_s* plan, const std::vector<int32_t>& rp,
 }
 
 int srt_tiles_apply(const srt_plan_s* plan, bool adjoint, int c0, int c1, int TG, const float* x,
-                    int64_t ldx, float* y, int64_t ldy, int ncols, cudaStream_t st) {
+                    int64_t ldx, float* y, int64_t ldy, int ncols, cudaStream_t st, int64_t ldn) {
   const srt_geometry& g = plan->g;
   const SrtTiles& t = adjoint ? plan->tla : plan->tlf;
   // float4 gathers and stores: 16-byte aligned rows of whole float4s
-  if (!t.ptr || c1 <= c0 || ncols <= 0 || ncols % 4 || ldx % 4 || ldy % 4 ||
-      (uintptr_t)x % 16 || (uintptr_t)y % 16 || ldx > 0x7fffffff)
+  if (!t.ptr || c1 <= c0 || ncols <= 0 || ncols % 4 || ldx % 4 || (ldn <= 0 && ldy % 4) ||
+      (uintptr_t)x % 16 || (uintptr_t)y % 16 || ldx > 0x7fffffff || ldn < 0)
     return SRT_ERR_ARG;
   if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 4;
+  if (ldn > 0) TG = 4;  // the fused reshape stages blocks of 8 x 4 output rows
   TileArgs A{t.ptr, t.off, t.nkeys, t.key0, adjoint ? g.n_zs : g.mz, c0, c1, g.n_ell, g.mz,
              (c1 - c0 + 1) / 2, t.pairs, TG,
-             srt_checked_rows(adjoint ? (int64_t)g.n_zs * g.n_ell : (int64_t)g.n_ell * g.mz)};
+             srt_checked_rows(adjoint ? (int64_t)g.n_zs * g.n_ell : (int64_t)g.n_ell * g.mz),
+             ldn};
   if (g.weight_dtype == SRT_BF16) {
     if (!t.w16) return SRT_ERR_ARG;
     const uint2* w = reinterpret_cast<const uint2*>(t.w16);

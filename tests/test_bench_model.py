@@ -57,3 +57,18 @@ def test_batch_scales_dense_bytes_and_flops():
     assert four["spmm2"]["flop"] == 4 * one["spmm2"]["flop"]
     entries = NNZ2 * 8 + 4 * 196_609
     assert four["spmm2"]["bytes"] - entries == 4 * (one["spmm2"]["bytes"] - entries)
+
+
+def test_fused_reshapes_model():
+    """With P2 and P1^-1 in the products' epilogues their stages drop out; the
+    products read and write the same compulsory bytes (the layout changes,
+    not the amount)."""
+    info = dict(nnz1=NNZ1, nnz2=NNZ2, a2_taps=1, n_taps=TAPS)
+    fused = bench.stage_model(G, info, 1, "fp32", fused=True)
+    plain = bench.stage_model(G, info, 1, "fp32")
+    assert [s and s[0] for s in fused["fwd"]] == ["spmm1", "permute1", "spmm2", None]
+    assert [s and s[0] for s in fused["adj"]] == ["permute2_inv", "spmm2t", None, "spmm1t"]
+    for d in ("fwd", "adj"):
+        for a, b in zip(fused[d], plain[d]):
+            if a is not None:
+                assert a == b
