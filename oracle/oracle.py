@@ -17,7 +17,10 @@ Parity status: every exported function is pinned by ``tests/test_oracle_*.py``:
 - coarea area sums;
 - the adjoint identity;
 - symmetries;
-- a hand-computed one-voxel case.
+- a hand-computed one-voxel case;
+- for the piecewise-linear voxels: partition of unity against the constant
+  basis, dense sampling of the interpolated function along circles, the walk
+  against the per-node box moments, and the adjoint identity.
 """
 from __future__ import annotations
 
@@ -53,16 +56,18 @@ class OracleGeometry:
     ell_lo: float
     ell_hi: float
     rho_linear: bool = False  # intermediate piecewise linear in rho (else constant on bins)
+    voxel_linear: bool = False  # f bilinear in (x, y) between voxel centres (else constant)
 
     @staticmethod
-    def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, phi0=0.0, rho_linear=False):
+    def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, phi0=0.0, rho_linear=False,
+                voxel_linear=False):
         """Default readings: rings at cell centres of the volume height and a
         radius grid covering [R - r_xy, R + r_xy], r_xy = ms*dxy/sqrt(2)."""
         h = mz * dz
         rxy = ms * dxy / math.sqrt(2.0)
         return OracleGeometry(ms, mz, float(dxy), float(dz), float(radius), n_phi, float(phi0),
                               n_zs, -0.5 * h, 0.5 * h, n_ell, radius - rxy, radius + rxy,
-                              bool(rho_linear))
+                              bool(rho_linear), bool(voxel_linear))
 
     @property
     def n_vox(self):
@@ -87,13 +92,13 @@ class _Geom(ctypes.Structure):
         ("n_phi", ctypes.c_int32), ("phi0", ctypes.c_double),
         ("n_zs", ctypes.c_int32), ("zs_lo", ctypes.c_double), ("zs_hi", ctypes.c_double),
         ("n_ell", ctypes.c_int32), ("ell_lo", ctypes.c_double), ("ell_hi", ctypes.c_double),
-        ("rho_linear", ctypes.c_int32),
+        ("rho_linear", ctypes.c_int32), ("voxel_linear", ctypes.c_int32),
     ]
 
 
 def _cg(g: OracleGeometry) -> _Geom:
     return _Geom(g.ms, g.mz, g.dxy, g.dz, g.radius, g.n_phi, g.phi0, g.n_zs, g.zs_lo, g.zs_hi,
-                 g.n_ell, g.ell_lo, g.ell_hi, int(g.rho_linear))
+                 g.n_ell, g.ell_lo, g.ell_hi, int(g.rho_linear), int(g.voxel_linear))
 
 
 def build(force: bool = False) -> str:
@@ -228,8 +233,9 @@ def shell_weights(g: OracleGeometry, j: int, h: int, m: int) -> dict:
 
 
 def circle_arcs(g: OracleGeometry, j: int, l: int) -> dict:
-    """In-plane circle (column j, bin-centre radius rho_l): {pixel: arc length}."""
-    cap = 4 * (g.ms + 1) + 4
+    """In-plane circle (column j, bin-centre radius rho_l): {pixel: arc length},
+    or with piecewise-linear voxels {node: integral of its basis}."""
+    cap = 4 * (8 * g.ms + 8) if g.voxel_linear else 4 * (g.ms + 1) + 4
     pix = np.zeros(cap, dtype=np.int32)
     ln = np.zeros(cap, dtype=np.float64)
     n = lib().orc_circle_arcs(ctypes.byref(_cg(g)), j, l, _iptr(pix), _dptr(ln), cap)

@@ -45,6 +45,21 @@
  * the weight int (rho - rho_l) ds / dl, with int ds = l_m dt and
  * int rho ds = l_m^2 (cos t0 - cos t1) along the semicircle rho = l_m sin t.
  *
+ * Piecewise-linear voxels (voxel_linear = 1; the same remark of the paper):
+ * in every slab, f is the bilinear interpolation in (x, y) of its values at
+ * the voxel centres (the nodes x_i = -hx + (i + 1/2) dxy), held constant in
+ * x beyond the first and the last node column (the outer half voxel on each
+ * side of the volume), likewise in y, and still constant along z within a
+ * slab.  Node i's basis along x is (x - x_{i-1})/dxy on [x_{i-1}, x_i] and
+ * (x_{i+1} - x)/dxy on [x_i, x_{i+1}], replaced by 1 on [-hx, x_0] for i = 0
+ * and on [x_{ms-1}, hx] for i = ms - 1; the in-plane weight of node
+ * (ix, iy) is the product of its x and y bases integrated along the circle.
+ * The circle walk then also breaks at the node lines x = x_i, y = y_i, so
+ * that every arc lies in one piece of the bases, and gives each of the (up
+ * to) four nodes of that piece the integral of its basis product over the
+ * arc, in closed form:
+ *   int_{a0}^{a1} (px + qx cos a)(py + qy sin a) rho da.
+ *
  * Layouts: f[ix][iy][iz] (z fastest), p[j][h][m].  All arithmetic is FP64.
  */
 #include <math.h>
@@ -68,6 +83,7 @@ typedef struct {
   int32_t n_ell;         /* radius bins shared by rho and l                */
   double ell_lo, ell_hi; /* radius grid range                              */
   int32_t rho_linear;    /* 1: f^{1,2} piecewise linear in rho (see above) */
+  int32_t voxel_linear;  /* 1: f bilinear in (x, y) between voxel centres   */
 } orc_geom;
 
 /* ---------------------------------------------------------------- helpers */
@@ -104,15 +120,26 @@ typedef struct {
   int cl[2];       /* cached circle: radius index, -1 */
 } orc_ws;
 
+/* Sizes of one in-plane circle walk: breakpoints (two per grid line met),
+ * and the (pixel or node, weight) entries it writes (one per arc, or up to
+ * four per arc with the piecewise-linear voxels, whose walk also breaks at
+ * the node lines). */
+static int walk_breaks(const orc_geom* g) {
+  return g->voxel_linear ? 8 * g->ms + 8 : 4 * (g->ms + 1) + 4;
+}
+static int walk_entries(const orc_geom* g) {
+  return g->voxel_linear ? 4 * walk_breaks(g) : walk_breaks(g);
+}
+
 static int ws_init(orc_ws* w, const orc_geom* g) {
   int nt = 2 * (g->mz + 1) + 2 * (g->n_ell + 2) + 4;
-  int na = 4 * (g->ms + 1) + 4;
+  int na = walk_breaks(g), ne = walk_entries(g);
   w->tb = (double*)malloc(sizeof(double) * nt);
   w->ab = (double*)malloc(sizeof(double) * na);
   int ok = w->tb && w->ab;
   for (int c = 0; c < 2; ++c) {
-    w->cpix[c] = (int*)malloc(sizeof(int) * na);
-    w->clen[c] = (double*)malloc(sizeof(double) * na);
+    w->cpix[c] = (int*)malloc(sizeof(int) * ne);
+    w->clen[c] = (double*)malloc(sizeof(double) * ne);
     w->cn[c] = 0;
     w->cl[c] = -1;
     ok = ok && w->cpix[c] && w->clen[c];
@@ -137,8 +164,12 @@ static void ws_free(orc_ws* w) {
  * line.  Each arc between consecutive breakpoints then lies in one pixel
  * (the one holding its midpoint).  Output: (pixel ix*ms+iy, arc length)
  * for arcs inside the grid.  Returns the number of arcs written.          */
+static int circle_walk_hat(const orc_geom* g, double sx, double sy, double rho, double* ab,
+                           int* pix, double* len);
+
 static int circle_walk(const orc_geom* g, double sx, double sy, double rho, double* ab,
                        int* pix, double* len) {
+  if (g->voxel_linear) return circle_walk_hat(g, sx, sy, rho, ab, pix, len);
   const double hx = half_x(g);
   int n = 0;
   for (int i = 0; i <= g->ms; ++i) {
@@ -178,6 +209,99 @@ static int circle_walk(const orc_geom* g, double sx, double sy, double rho, doub
     pix[out] = ix * g->ms + iy;
     len[out] = rho * (a1 - a0);
     ++out;
+  }
+  return out;
+}
+
+/* One axis of the piecewise-linear voxels at coordinate u (x or y): the
+ * nodes whose basis is non-zero there (1 or 2) and each basis as
+ * a + b u.  Node centres -hx + (i + 1/2) d. */
+static int axis_pieces(const orc_geom* g, double u, int* node, double* a, double* b) {
+  const double hx = half_x(g), d = g->dxy;
+  const double s = (u + hx) / d - 0.5; /* node coordinate: node i at s = i */
+  if (s <= 0.0 || g->ms == 1) {
+    node[0] = 0;
+    a[0] = 1.0;
+    b[0] = 0.0;
+    return 1;
+  }
+  if (s >= g->ms - 1) {
+    node[0] = g->ms - 1;
+    a[0] = 1.0;
+    b[0] = 0.0;
+    return 1;
+  }
+  int i = (int)floor(s);
+  if (i > g->ms - 2) i = g->ms - 2;
+  const double x0 = -hx + (i + 0.5) * d, x1 = x0 + d;
+  node[0] = i; /* (x1 - u) / d */
+  a[0] = x1 / d;
+  b[0] = -1.0 / d;
+  node[1] = i + 1; /* (u - x0) / d */
+  a[1] = -x0 / d;
+  b[1] = 1.0 / d;
+  return 2;
+}
+
+/* Circle walk of the piecewise-linear voxels: breakpoints at the pixel
+ * lines and the node lines; on each arc [a0, a1] the bases are
+ * ax + bx x and ay + by y with x = sx + rho cos a, y = sy + rho sin a, so
+ * node (i, k) gets rho * int (px + qx cos a)(py + qy sin a) da with
+ * px = ax + bx sx, qx = bx rho (likewise y), whose terms integrate to
+ *   px py (a1 - a0) + px qy (cos a0 - cos a1) + qx py (sin a1 - sin a0)
+ *   + qx qy (sin^2 a1 - sin^2 a0) / 2
+ * (the differences taken as products of sines and cosines of the half sum
+ * and half difference).  Arcs outside the volume carry no weight. */
+static int circle_walk_hat(const orc_geom* g, double sx, double sy, double rho, double* ab,
+                           int* pix, double* len) {
+  const double hx = half_x(g), hd = 0.5 * g->dxy;
+  int n = 0;
+  for (int i = 0; i <= 2 * g->ms; ++i) {
+    double u = -hx + i * hd - sx; /* pixel line (i even) or node line (i odd) */
+    if (fabs(u) <= rho) {
+      double v = sqrt((rho - u) * (rho + u));
+      ab[n++] = wrap_2pi(atan2(v, u));
+      ab[n++] = wrap_2pi(atan2(-v, u));
+    }
+  }
+  for (int i = 0; i <= 2 * g->ms; ++i) {
+    double u = -hx + i * hd - sy;
+    if (fabs(u) <= rho) {
+      double v = sqrt((rho - u) * (rho + u));
+      ab[n++] = wrap_2pi(atan2(u, v));
+      ab[n++] = wrap_2pi(atan2(u, -v));
+    }
+  }
+  qsort(ab, n, sizeof(double), cmp_double);
+  int out = 0;
+  int nseg = n > 0 ? n : 1;
+  for (int s = 0; s < nseg; ++s) {
+    double a0, a1;
+    if (n == 0) {
+      a0 = 0.0;
+      a1 = 2.0 * ORC_PI;
+    } else {
+      a0 = ab[s];
+      a1 = (s + 1 < n) ? ab[s + 1] : ab[0] + 2.0 * ORC_PI;
+    }
+    if (!(a1 > a0)) continue;
+    const double am = 0.5 * (a0 + a1), ah = 0.5 * (a1 - a0);
+    const double x = sx + rho * cos(am), y = sy + rho * sin(am);
+    if (!(x > -hx && x < hx && y > -hx && y < hx)) continue;
+    int nx[2], ny[2];
+    double ax[2], bx[2], ay[2], by[2];
+    const int cx = axis_pieces(g, x, nx, ax, bx), cy = axis_pieces(g, y, ny, ay, by);
+    const double dcos = 2.0 * sin(am) * sin(ah);         /* cos a0 - cos a1 */
+    const double dsin = 2.0 * cos(am) * sin(ah);         /* sin a1 - sin a0 */
+    const double dsq = 0.5 * sin(2.0 * am) * sin(2.0 * ah); /* (sin^2 a1 - sin^2 a0) / 2 */
+    for (int p = 0; p < cx; ++p)
+      for (int q = 0; q < cy; ++q) {
+        const double px = ax[p] + bx[p] * sx, qx = bx[p] * rho;
+        const double py = ay[q] + by[q] * sy, qy = by[q] * rho;
+        pix[out] = nx[p] * g->ms + ny[q];
+        len[out] = rho * (px * py * (a1 - a0) + px * qy * dcos + qx * py * dsin + qx * qy * dsq);
+        ++out;
+      }
   }
   return out;
 }
@@ -509,14 +633,16 @@ long orc_shell_contrib(const orc_geom* g, int j, int h, int m, long* vox, double
 }
 
 /* In-plane circle of sensor column j at bin-centre radius rho_l: arcs per
- * pixel, in walk order (a pixel may appear twice).                        */
+ * pixel, in walk order (a pixel may appear twice); with the piecewise-linear
+ * voxels, the basis integrals per node (a node appears once per arc of its
+ * support).                                                               */
 int orc_circle_arcs(const orc_geom* g, int j, int l, int32_t* pix, double* len, int cap) {
   if (check_geom(g)) return -1;
-  int na = 4 * (g->ms + 1) + 4;
-  if (cap < na) return -3;
+  int na = walk_breaks(g), ne = walk_entries(g);
+  if (cap < ne) return -3;
   double* ab = (double*)malloc(sizeof(double) * na);
   if (!ab) return -2;
-  int* p = (int*)malloc(sizeof(int) * na);
+  int* p = (int*)malloc(sizeof(int) * ne);
   int n = circle_walk(g, sensor_x(g, j), sensor_y(g, j), ell_centre(g, l), ab, p, len);
   for (int i = 0; i < n; ++i) pix[i] = p[i];
   free(p);
@@ -621,6 +747,111 @@ double orc_arc_in_box(double cx, double cy, double r, double x0, double x1, doub
   return arc_in_box(cx, cy, r, x0, x1, y0, y1);
 }
 
+/* Length and moments of the circle (cx, cy, r) inside the box, from the same
+ * breakpoints and midpoint test as arc_in_box: m[0] = int ds, m[1] = int x ds,
+ * m[2] = int y ds, m[3] = int x y ds, with, per arc [a0, a1],
+ *   int x ds  = r cx (a1 - a0) + r^2 (sin a1 - sin a0),
+ *   int y ds  = r cy (a1 - a0) + r^2 (cos a0 - cos a1),
+ *   int xy ds = r cx cy (a1 - a0) + r^2 cx (cos a0 - cos a1)
+ *               + r^2 cy (sin a1 - sin a0) + r^3 (sin^2 a1 - sin^2 a0) / 2. */
+static void arc_moments_in_box(double cx, double cy, double r, double x0, double x1, double y0,
+                               double y1, double* m) {
+  double ab[8];
+  int n = 0;
+  double xs[2] = {x0, x1}, ys[2] = {y0, y1};
+  for (int i = 0; i < 2; ++i) {
+    double u = xs[i] - cx;
+    if (fabs(u) <= r) {
+      double v = sqrt((r - u) * (r + u));
+      ab[n++] = wrap_2pi(atan2(v, u));
+      ab[n++] = wrap_2pi(atan2(-v, u));
+    }
+    u = ys[i] - cy;
+    if (fabs(u) <= r) {
+      double v = sqrt((r - u) * (r + u));
+      ab[n++] = wrap_2pi(atan2(u, v));
+      ab[n++] = wrap_2pi(atan2(u, -v));
+    }
+  }
+  qsort(ab, n, sizeof(double), cmp_double);
+  m[0] = m[1] = m[2] = m[3] = 0.0;
+  int nseg = n > 0 ? n : 1;
+  for (int s = 0; s < nseg; ++s) {
+    double a0, a1;
+    if (n == 0) {
+      a0 = 0.0;
+      a1 = 2.0 * ORC_PI;
+    } else {
+      a0 = ab[s];
+      a1 = (s + 1 < n) ? ab[s + 1] : ab[0] + 2.0 * ORC_PI;
+    }
+    if (!(a1 > a0)) continue;
+    const double am = 0.5 * (a0 + a1), ah = 0.5 * (a1 - a0);
+    const double x = cx + r * cos(am), y = cy + r * sin(am);
+    if (!(x > x0 && x < x1 && y > y0 && y < y1)) continue;
+    const double dcos = 2.0 * sin(am) * sin(ah), dsin = 2.0 * cos(am) * sin(ah);
+    const double dsq = 0.5 * sin(2.0 * am) * sin(2.0 * ah);
+    m[0] += r * (a1 - a0);
+    m[1] += r * cx * (a1 - a0) + r * r * dsin;
+    m[2] += r * cy * (a1 - a0) + r * r * dcos;
+    m[3] += r * cx * cy * (a1 - a0) + r * r * (cx * dcos + cy * dsin) + r * r * r * dsq;
+  }
+}
+
+/* One side of node i's basis along an axis: the interval [u0, u1] and the
+ * basis a + b u on it (side 0: below the node, side 1: above).  Returns 0
+ * where the side is empty. */
+static int node_side(const orc_geom* g, int i, int side, double* u0, double* u1, double* a,
+                     double* b) {
+  const double hx = half_x(g), d = g->dxy, xc = -hx + (i + 0.5) * d;
+  if (side == 0) {
+    if (i == 0) { /* margin: constant 1 from the volume's edge */
+      *u0 = -hx;
+      *u1 = xc;
+      *a = 1.0;
+      *b = 0.0;
+    } else { /* (u - x_{i-1}) / d */
+      *u0 = xc - d;
+      *u1 = xc;
+      *a = -(xc - d) / d;
+      *b = 1.0 / d;
+    }
+  } else {
+    if (i == g->ms - 1) {
+      *u0 = xc;
+      *u1 = hx;
+      *a = 1.0;
+      *b = 0.0;
+    } else { /* (x_{i+1} - u) / d */
+      *u0 = xc;
+      *u1 = xc + d;
+      *a = (xc + d) / d;
+      *b = -1.0 / d;
+    }
+  }
+  return *u1 > *u0;
+}
+
+/* In-plane weight of node (ix, iy) on the circle (sx, sy, rho), piecewise-
+ * linear voxels: over the four boxes of its support (sides of x times sides
+ * of y), int (ax + bx x)(ay + by y) ds = ax ay L + ax by My + bx ay Mx
+ * + bx by Mxy from the box moments. */
+static double node_plane_weight(const orc_geom* g, double sx, double sy, double rho, int ix,
+                                int iy) {
+  double acc = 0.0;
+  for (int p = 0; p < 2; ++p) {
+    double x0, x1, ax, bx;
+    if (!node_side(g, ix, p, &x0, &x1, &ax, &bx)) continue;
+    for (int q = 0; q < 2; ++q) {
+      double y0, y1, ay, by, m[4];
+      if (!node_side(g, iy, q, &y0, &y1, &ay, &by)) continue;
+      arc_moments_in_box(sx, sy, rho, x0, x1, y0, y1, m);
+      acc += ax * ay * m[0] + ax * by * m[2] + bx * ay * m[1] + bx * by * m[3];
+    }
+  }
+  return acc;
+}
+
 /* Weight of the intermediate's value at (slab k, radius l) in the (z, rho)
  * semicircle (centre (zc, 0), radius ell): piecewise constant, the arc in the
  * cell [z0, z0 + dz] x [bin l]; piecewise linear, the hat of node rho_l
@@ -658,14 +889,23 @@ static double point_weight(const orc_geom* g, int j, int h, int m, int ix, int i
   const double hx = half_x(g), hz = half_z(g), dl = dell(g);
   const double sx = sensor_x(g, j), sy = sensor_y(g, j);
   const double ell = ell_centre(g, m), zc = ring_z(g, h);
-  const double px0 = -hx + ix * g->dxy, py0 = -hx + iy * g->dxy;
+  /* the pixel, or with the piecewise-linear voxels the node's support (the
+   * pixel widened by half a voxel on each side inside the volume) */
+  double px0 = -hx + ix * g->dxy, py0 = -hx + iy * g->dxy;
+  double px1 = px0 + g->dxy, py1 = py0 + g->dxy;
+  if (g->voxel_linear) {
+    px0 = fmax(-hx, px0 - 0.5 * g->dxy);
+    px1 = fmin(hx, px1 + 0.5 * g->dxy);
+    py0 = fmax(-hx, py0 - 0.5 * g->dxy);
+    py1 = fmin(hx, py1 + 0.5 * g->dxy);
+  }
   const double z0 = -hz + k * g->dz;
-  /* in-plane distance range from the sensor to the pixel: only bins whose
-   * centre radius lies in it (plus one bin of margin) can meet the pixel */
-  double cx = fmax(px0 - sx, fmax(0.0, sx - (px0 + g->dxy)));
-  double cy = fmax(py0 - sy, fmax(0.0, sy - (py0 + g->dxy)));
-  double fx = fmax(fabs(px0 - sx), fabs(px0 + g->dxy - sx));
-  double fy = fmax(fabs(py0 - sy), fabs(py0 + g->dxy - sy));
+  /* in-plane distance range from the sensor to the box: only bins whose
+   * centre radius lies in it (plus one bin of margin) can meet the box */
+  double cx = fmax(px0 - sx, fmax(0.0, sx - px1));
+  double cy = fmax(py0 - sy, fmax(0.0, sy - py1));
+  double fx = fmax(fabs(px0 - sx), fabs(px1 - sx));
+  double fy = fmax(fabs(py0 - sy), fabs(py1 - sy));
   int l0 = (int)floor((sqrt(cx * cx + cy * cy) - g->ell_lo) / dl) - 1;
   int l1 = (int)floor((sqrt(fx * fx + fy * fy) - g->ell_lo) / dl) + 1;
   if (l0 < 0) l0 = 0;
@@ -673,7 +913,8 @@ static double point_weight(const orc_geom* g, int j, int h, int m, int ix, int i
   double acc = 0.0;
   for (int l = l0; l <= l1; ++l) {
     double rho = ell_centre(g, l);
-    double a1 = arc_in_box(sx, sy, rho, px0, px0 + g->dxy, py0, py0 + g->dxy);
+    double a1 = g->voxel_linear ? node_plane_weight(g, sx, sy, rho, ix, iy)
+                                : arc_in_box(sx, sy, rho, px0, px1, py0, py1);
     if (a1 == 0.0) continue;
     acc += a1 * semicircle_weight(g, zc, ell, z0, l);
   }
@@ -696,19 +937,27 @@ int orc_adjoint_voxels(const orc_geom* g, const double* p, const int32_t* voxels
 #pragma omp parallel for schedule(dynamic, 1)
   for (long i = 0; i < n; ++i) {
     int ix = voxels[3 * i], iy = voxels[3 * i + 1], k = voxels[3 * i + 2];
+    /* the voxel's box, or the node's support (piecewise-linear voxels) */
     double bx0 = -hx + ix * g->dxy, by0 = -hx + iy * g->dxy, bz0 = -hz + k * g->dz;
+    double bx1 = bx0 + g->dxy, by1 = by0 + g->dxy;
+    if (g->voxel_linear) {
+      bx0 = fmax(-hx, bx0 - 0.5 * g->dxy);
+      bx1 = fmin(hx, bx1 + 0.5 * g->dxy);
+      by0 = fmax(-hx, by0 - 0.5 * g->dxy);
+      by1 = fmin(hx, by1 + 0.5 * g->dxy);
+    }
     double acc = 0.0;
     for (int j = 0; j < g->n_phi; ++j) {
       double sx = sensor_x(g, j), sy = sensor_y(g, j);
       for (int h = 0; h < g->n_zs; ++h) {
         double zc = ring_z(g, h);
         /* distance range from the sensor point to the voxel box */
-        double cx = fmax(bx0 - sx, fmax(0.0, sx - (bx0 + g->dxy)));
-        double cy = fmax(by0 - sy, fmax(0.0, sy - (by0 + g->dxy)));
+        double cx = fmax(bx0 - sx, fmax(0.0, sx - bx1));
+        double cy = fmax(by0 - sy, fmax(0.0, sy - by1));
         double cz = fmax(bz0 - zc, fmax(0.0, zc - (bz0 + g->dz)));
         double dmin = sqrt(cx * cx + cy * cy + cz * cz);
-        double fx = fmax(fabs(bx0 - sx), fabs(bx0 + g->dxy - sx));
-        double fy = fmax(fabs(by0 - sy), fabs(by0 + g->dxy - sy));
+        double fx = fmax(fabs(bx0 - sx), fabs(bx1 - sx));
+        double fy = fmax(fabs(by0 - sy), fabs(by1 - sy));
         double fz = fmax(fabs(bz0 - zc), fabs(bz0 + g->dz - zc));
         double dmax = sqrt(fx * fx + fy * fy + fz * fz);
         int m0 = (int)floor((dmin - g->ell_lo) / dl) - 1;
