@@ -46,6 +46,8 @@ def parse():
                    help="store A1 for a quarter of the sensor columns (quarter turns only, no mirror)")
     p.add_argument("--rowwise", action="store_true",
                    help="every product a warp per output row (else register tiles of rows)")
+    p.add_argument("--voxel-linear", action="store_true",
+                   help="f bilinear in (x, y) between voxel centres (else constant on voxels)")
     p.add_argument("--fuse-reshapes", action="store_true",
                    help="P2 and P1^-1 folded into the A2 / A2^T tile products")
     p.add_argument("--a1-full", action="store_true",
@@ -258,14 +260,14 @@ def workload_config(name, geom, batch, weights, extra=None):
     return cfg
 
 
-def cpu_oracle_rate(name, budget_s, seed=5, rho_linear=False):
+def cpu_oracle_rate(name, budget_s, seed=5, rho_linear=False, voxel_linear=False):
     """Oracle forward + adjoint on a seeded shell sample sized to budget_s;
     returns (pairs/s extrapolated to the full workload, threads, sample text)."""
     import numpy as np
     from oracle import oracle as O
     from paper_2402_15641_gb300 import inputs as I
     sz = I.sizes(name)
-    g = O.OracleGeometry.default(**sz, rho_linear=rho_linear)
+    g = O.OracleGeometry.default(**sz, rho_linear=rho_linear, voxel_linear=voxel_linear)
     f = I.phantom(name)
     y = I.probe(name)
     total = g.n_phi * g.n_zs * g.n_ell
@@ -303,7 +305,8 @@ def run_reference(args):
     from paper_2402_15641_gb300 import inputs as I
     import numpy as np
     sz = I.sizes(args.workload)
-    g = O.OracleGeometry.default(**sz, rho_linear=args.rho_linear)
+    g = O.OracleGeometry.default(**sz, rho_linear=args.rho_linear,
+                                 voxel_linear=args.voxel_linear)
     f = I.phantom(args.workload)
     y = I.probe(args.workload)
     total = g.n_phi * g.n_zs * g.n_ell
@@ -363,7 +366,8 @@ def run_ours(args):
     geom = Geometry.from_sizes(sz, weight_dtype=args.weights, csr_only=args.csr_only,
                                a1_rotation=args.a1_rotation, rho_linear=args.rho_linear,
                                rowwise=args.rowwise, a1_full=args.a1_full,
-                               fuse_reshapes=args.fuse_reshapes)
+                               fuse_reshapes=args.fuse_reshapes,
+                               voxel_linear=args.voxel_linear)
     B = args.batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -546,11 +550,15 @@ def run_ours(args):
                                                    "four reshape kernels"),
                                       "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3),
                                       "intermediate": ("piecewise linear in rho" if args.rho_linear
-                                                       else "piecewise constant on radius bins")}),
+                                                       else "piecewise constant on radius bins"),
+                                      "voxels": ("bilinear in (x, y) between voxel centres"
+                                                 if args.voxel_linear
+                                                 else "piecewise constant")}),
            "roofline": roof, "hbm": hbm, "stages": stages, "clocks": clk, "e2e": e2e,
            "gpu_launches": launches}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, n, t = cpu_oracle_rate(args.workload, 15.0, rho_linear=args.rho_linear)
+        rate, cores, n, t = cpu_oracle_rate(args.workload, 15.0, rho_linear=args.rho_linear,
+                                            voxel_linear=args.voxel_linear)
         out["cpu_baseline"] = {
             "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle forward + adjoint over {n} seeded shells of "

@@ -87,6 +87,16 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  * separate 16- or 32-byte piece, which costs the products more than the
  * separate reshape kernels (which run at HBM speed) cost. */
 #define SRT_FUSE_RESHAPES 0x80
+/* SRT_VOXEL_LINEAR: the volume is piecewise linear in x and y instead of
+ * constant on the voxels (Sec. 3.1 notes the method carries over to other
+ * bases): in every slab, f is the bilinear interpolation of its values at
+ * the voxel centres, held constant across the outer half voxel at each side
+ * of the volume, and still constant along z within a slab.  A1's entry
+ * ((j, l), node (ix, iy)) becomes the node's basis integrated along the
+ * circle; A1 holds more entries (each node's support is 2 x 2 voxels), the
+ * layouts and every kernel stay the same, and f is read and written as the
+ * node values. */
+#define SRT_VOXEL_LINEAR 0x100
 /* When the rings are spaced like the slabs ((zs_hi - zs_lo) / n_zs = dz, any
  * n_zs, any offset; e.g. n_zs = mz over the volume height), ring h sits at
  * slab h + s plus a fixed fraction of a slab, A2[(h,m),(l,k)] = T[m, k-h-s, l]

@@ -21,6 +21,7 @@ SRT_RHO_LINEAR = 16
 SRT_ROWWISE = 32
 SRT_A1_FULL = 64
 SRT_FUSE_RESHAPES = 128
+SRT_VOXEL_LINEAR = 256
 SRT_NOALLOC_WORKSPACE_BYTES = 32 << 20
 
 

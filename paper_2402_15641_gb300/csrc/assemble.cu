@@ -38,6 +38,7 @@ struct GeomDev {
   int nj;       // sensor columns whose A1 rows are assembled (the first nj of n_phi)
   int jfirst, ntot;  // column j sits at angle phi0 + 2 pi (jfirst + j) / ntot
   int rho_lin;  // A2 columns are hats of the radius nodes (else bins)
+  int vox_lin;  // A1 columns are bilinear hats of the voxel centres (else pixels)
   double dxy, dz, radius, phi0, zs_lo, zs_hi, ell_lo, ell_hi;
   double hx, hz, dl, thr1, thr2;
 };
@@ -51,6 +52,7 @@ GeomDev make_geom(const srt_geometry& g) {
   G.jfirst = g.n_phi_total > 0 ? g.phi_first : 0;
   G.ntot = g.n_phi_total > 0 ? g.n_phi_total : g.n_phi;
   G.rho_lin = (g.flags & SRT_RHO_LINEAR) ? 1 : 0;
+  G.vox_lin = (g.flags & SRT_VOXEL_LINEAR) ? 1 : 0;
   G.n_zs = g.n_zs;
   G.n_ell = g.n_ell;
   G.dxy = g.dxy;
@@ -105,6 +107,33 @@ __device__ double hat_weight(const GeomDev& G, double zc, double r, int l, doubl
   return w;
 }
 
+// Piecewise-linear voxels: node (i, k) at the voxel centre (x_i, y_k) has the
+// basis (1 + bx (x - x_i))(1 + by (y - y_k)) on each of the four boxes of its
+// support, bx = 1/dxy below the node and -1/dxy above it; at the volume's
+// edge the outer half voxel holds the edge node's value (basis 1, bx = 0).
+// The weight is the basis integrated along the circle (centre (cx, cy),
+// radius r) over those boxes, in coordinates centred on the node.
+__device__ double node_weight(const GeomDev& G, double cx, double cy, double r, int i, int k) {
+  const double d = G.dxy;
+  const double xn = -G.hx + (i + 0.5) * d, yn = -G.hx + (k + 0.5) * d;
+  const double cxr = cx - xn, cyr = cy - yn;
+  double w = 0.0;
+  for (int p = 0; p < 2; ++p) {
+    const bool edge_x = p == 0 ? i == 0 : i == G.ms - 1;
+    const double xa = p == 0 ? (edge_x ? -0.5 * d : -d) : 0.0;
+    const double xb = p == 0 ? 0.0 : (edge_x ? 0.5 * d : d);
+    const double bx = edge_x ? 0.0 : (p == 0 ? 1.0 / d : -1.0 / d);
+    for (int q = 0; q < 2; ++q) {
+      const bool edge_y = q == 0 ? k == 0 : k == G.ms - 1;
+      const double ya = q == 0 ? (edge_y ? -0.5 * d : -d) : 0.0;
+      const double yb = q == 0 ? 0.0 : (edge_y ? 0.5 * d : d);
+      const double by = edge_y ? 0.0 : (q == 0 ? 1.0 / d : -1.0 / d);
+      w += srt_arc_bilinear(cxr, cyr, r, xa, xb, ya, yb, bx, by);
+    }
+  }
+  return w;
+}
+
 // Enumerate one strip.  The strip spans [s0, s1] along the strip axis; the
 // circle (centre (cu, cv) in (strip axis, cross axis), radius r) has two
 // branches over it.  For every candidate cross index q (ascending) the exact
@@ -114,9 +143,15 @@ template <bool A1, class F>
 __device__ int strip_enum(const GeomDev& G, double cu, double cv, double r, int s, int& drop, F f) {
   double s0, s1, half, d;
   int n;
-  if (A1) {  // strip = pixel column ix, cross axis = y
+  if (A1 && !G.vox_lin) {  // strip = pixel column ix, cross axis = y
     s0 = -G.hx + s * G.dxy;
     s1 = -G.hx + (s + 1) * G.dxy;
+    half = G.hx;
+    d = G.dxy;
+    n = G.ms;
+  } else if (A1) {  // strip = support of node column i (half a voxel at the edges)
+    s0 = s == 0 ? -G.hx : -G.hx + (s - 0.5) * G.dxy;
+    s1 = s == G.ms - 1 ? G.hx : -G.hx + (s + 1.5) * G.dxy;
     half = G.hx;
     d = G.dxy;
     n = G.ms;
@@ -142,6 +177,10 @@ __device__ int strip_enum(const GeomDev& G, double cu, double cv, double r, int 
   int a0, a1, b0, b1;
   cover(cv - thi, cv - tlo, half, d, n, a0, a1);
   cover(cv + tlo, cv + thi, half, d, n, b0, b1);
+  if (A1 && G.vox_lin) {  // node supports reach a voxel further down
+    a0 = a0 > 0 ? a0 - 1 : 0;
+    b0 = b0 > 0 ? b0 - 1 : 0;
+  }
   if (b0 <= a1) b0 = a1 + 1;  // union, ascending
   const double thr = A1 ? G.thr1 : G.thr2;
   int kept = 0;
@@ -150,7 +189,9 @@ __device__ int strip_enum(const GeomDev& G, double cu, double cv, double r, int 
     for (int q = q0; q <= q1; ++q) {
       const double c0 = -half + q * d, c1 = -half + (q + 1) * d;
       double w;
-      if (A1)
+      if (A1 && G.vox_lin)
+        w = node_weight(G, cu, cv, r, s, q);
+      else if (A1)
         w = srt_arc_in_rect(cu, cv, r, s0, s1, c0, c1);
       else if (!G.rho_lin)  // (z, rho) plane: x = z, y = rho
         w = srt_arc_in_rect(cv, cu, r, c0, c1, s0, s1);

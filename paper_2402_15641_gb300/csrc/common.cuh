@@ -278,6 +278,53 @@ __host__ __device__ inline double srt_arc_in_rect_m(double cx, double cy, double
   return r * t;
 }
 
+// int (1 + bx x)(1 + by y) ds along the circle (cx, cy, r) inside the box
+// [x0, x1] x [y0, y1], in coordinates centred on a node of the piecewise-
+// linear voxels (so x, y and the result stay small).  On each quarter
+// interval [t0, t1] = tm -/+ h, with x = X0 + r C (cos s - 1) - r S sin s and
+// y = Y0 + r S (cos s - 1) + r C sin s (C = cos tm, S = sin tm, (X0, Y0) the
+// interval's midpoint, s in [-h, h]):
+//   int ds    = 2 h r
+//   int x ds  = r (2 h X0 + r C Ic)
+//   int y ds  = r (2 h Y0 + r S Ic)
+//   int xy ds = r (2 h X0 Y0 + r (X0 S + Y0 C) Ic + r^2 C S Id)
+// with Ic = int (cos s - 1) ds = 2 (sin h - h) and Id = int (cos s - 1)^2 -
+// sin^2 s ds = 2 h + sin 2h - 4 sin h over [-h, h] (odd terms vanish),
+// taken from their Taylor series for h < 0.05, where the closed forms
+// cancel (truncation below 1e-12 relative).
+__host__ __device__ inline double srt_arc_bilinear(double cx, double cy, double r, double x0,
+                                                   double x1, double y0, double y1, double bx,
+                                                   double by) {
+  const double hp = 0.5 * SRT_PI;
+  const double a1 = srt_acos_r(x1 - cx, r), a0 = srt_acos_r(x0 - cx, r);
+  const double s0 = srt_asin_r(y0 - cy, r), s1 = srt_asin_r(y1 - cy, r);
+  const double lo[4] = {fmax(0.0, fmax(a1, s0)), fmax(hp, fmax(a1, SRT_PI - s1)),
+                        fmax(-SRT_PI, fmax(-a0, -SRT_PI - s1)), fmax(-hp, fmax(-a0, s0))};
+  const double hi[4] = {fmin(hp, fmin(a0, s1)), fmin(SRT_PI, fmin(a0, SRT_PI - s0)),
+                        fmin(-hp, fmin(-a1, -SRT_PI - s0)), fmin(0.0, fmin(-a1, s1))};
+  double acc = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    if (!(hi[i] > lo[i])) continue;
+    const double tm = 0.5 * (lo[i] + hi[i]), h = 0.5 * (hi[i] - lo[i]);
+    const double C = cos(tm), S = sin(tm);
+    const double X0 = cx + r * C, Y0 = cy + r * S;
+    double ic, id;
+    if (h < 0.05) {
+      const double h2 = h * h, h3 = h2 * h;
+      ic = h3 * (-1.0 / 3.0 + h2 * (1.0 / 60.0 - h2 / 2520.0));
+      id = h3 * (-2.0 / 3.0 + h2 * (7.0 / 30.0 - h2 * 31.0 / 1260.0));
+    } else {
+      ic = 2.0 * (sin(h) - h);
+      id = 2.0 * h + sin(2.0 * h) - 4.0 * sin(h);
+    }
+    const double L = 2.0 * h;
+    const double mx = L * X0 + r * C * ic, my = L * Y0 + r * S * ic;
+    const double mxy = L * X0 * Y0 + r * (X0 * S + Y0 * C) * ic + r * r * C * S * id;
+    acc += r * (L + bx * mx + by * my + bx * by * mxy);
+  }
+  return acc;
+}
+
 // Round an FP64 value to BF16 (round to nearest, ties to even) in one step,
 // from the FP64 bit pattern: keep 7 fraction bits, round on the other 45.
 // Values below the BF16 normal range flush to signed zero (entries here are

@@ -46,12 +46,13 @@ class Geometry:
     phi_first: int = 0
     a1_full: bool = False  # store A1 for every column (else for the aperture's symmetry set)
     fuse_reshapes: bool = False  # P2 / P1^-1 folded into the A2 / A2^T tiles
+    voxel_linear: bool = False  # f bilinear in (x, y) between voxel centres (else constant)
 
     @staticmethod
     def default(ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, **options) -> "Geometry":
         """Default readings, computed by the library (srt_geometry_default);
         options set weight_dtype / keep_f64 / csr_only / a1_rotation / rho_linear /
-        rowwise / a1_full / fuse_reshapes."""
+        rowwise / a1_full / fuse_reshapes / voxel_linear."""
         g = L.SrtGeometry()
         check(L.lib().srt_geometry_default(ctypes.byref(g), ms, mz, dxy, dz, radius, n_phi, n_zs,
                                            n_ell), "srt_geometry_default")
@@ -83,7 +84,8 @@ class Geometry:
                              | (L.SRT_RHO_LINEAR if self.rho_linear else 0)
                              | (L.SRT_ROWWISE if self.rowwise else 0)
                              | (L.SRT_A1_FULL if self.a1_full else 0)
-                             | (L.SRT_FUSE_RESHAPES if self.fuse_reshapes else 0),
+                             | (L.SRT_FUSE_RESHAPES if self.fuse_reshapes else 0)
+                             | (L.SRT_VOXEL_LINEAR if self.voxel_linear else 0),
                              self.n_phi_total, self.phi_first)
 
     @property

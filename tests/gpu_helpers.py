@@ -8,7 +8,7 @@ import numpy as np
 
 def geom_pair(orc, ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, phi0=0.0, zs=None, ell=None,
               weight_dtype="fp32", keep_f64=False, csr_only=False, a1_rotation=False,
-              rho_linear=False, rowwise=False, a1_full=False):
+              rho_linear=False, rowwise=False, a1_full=False, voxel_linear=False):
     """The same explicit geometry for the CUDA plan and for the oracle."""
     from paper_2402_15641_gb300.srt import Geometry
     h = mz * dz
@@ -18,10 +18,10 @@ def geom_pair(orc, ms, mz, dxy, dz, radius, n_phi, n_zs, n_ell, phi0=0.0, zs=Non
     g = Geometry(ms, mz, float(dxy), float(dz), float(radius), n_phi, float(phi0), n_zs,
                  float(zs_lo), float(zs_hi), n_ell, float(ell_lo), float(ell_hi),
                  weight_dtype, keep_f64, csr_only, a1_rotation, rho_linear, rowwise,
-                 a1_full=a1_full)
+                 a1_full=a1_full, voxel_linear=voxel_linear)
     o = orc.OracleGeometry(ms, mz, float(dxy), float(dz), float(radius), n_phi, float(phi0), n_zs,
                            float(zs_lo), float(zs_hi), n_ell, float(ell_lo), float(ell_hi),
-                           bool(rho_linear))
+                           bool(rho_linear), bool(voxel_linear))
     return g, o
 
 

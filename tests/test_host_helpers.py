@@ -118,3 +118,73 @@ def test_arc_length_against_oracle_walk_at_degenerate_positions(run, orc):
     for c, (length, _, _) in zip(cases, vals):
         want = orc.arc_in_box(*c)
         assert abs(length - want) <= 1e-12 * max(1.0, c[2]), (c, length, want)
+
+
+def _bilinear_quadrature(cx, cy, r, x0, x1, y0, y1, bx, by, order=10):
+    """int (1 + bx x)(1 + by y) ds along the circle inside the box: numpy's
+    Gauss-Legendre rule on the sub-arcs between the angles where the circle
+    meets a box line (the integrand is smooth on each)."""
+    ang = [0.0, 2 * math.pi]
+    for c, lines, off in ((cx, (x0, x1), 0.0), (cy, (y0, y1), 0.5 * math.pi)):
+        for v in lines:
+            u = v - c
+            if abs(u) <= r:
+                b = math.acos(max(-1.0, min(1.0, u / r)))
+                ang += [(b + off) % (2 * math.pi), (-b + off) % (2 * math.pi)]
+    ang = np.unique(np.array(ang))
+    t, w = np.polynomial.legendre.leggauss(order)
+    total = 0.0
+    for a0, a1 in zip(ang[:-1], ang[1:]):
+        am, ah = 0.5 * (a0 + a1), 0.5 * (a1 - a0)
+        xm, ym = cx + r * math.cos(am), cy + r * math.sin(am)
+        if not (x0 < xm < x1 and y0 < ym < y1):
+            continue
+        a = am + ah * t
+        x, y = cx + r * np.cos(a), cy + r * np.sin(a)
+        total += float(np.sum(w * (1 + bx * x) * (1 + by * y))) * ah * r
+    return total
+
+
+def test_arc_bilinear_against_quadrature(run):
+    """srt_arc_bilinear (the piecewise-linear voxels' entries, node-centred
+    coordinates) against Gauss-Legendre quadrature: random circles through
+    the four boxes of a node's support and its half-width margin boxes, with
+    the slopes those boxes use (+-1/d, 0), short arcs where the series
+    apply, and random boxes and slopes."""
+    rng = np.random.default_rng(21)
+    cases = []
+    for _ in range(1500):
+        d = float(rng.choice([0.1, 0.5, 1.3]))
+        r = float(rng.uniform(0.5, 40.0))
+        ang = rng.uniform(0, 2 * math.pi)
+        dist = r + rng.uniform(-1.5, 1.5) * d  # the circle passes near the node
+        cx, cy = -dist * math.cos(ang), -dist * math.sin(ang)
+        sx, sy = int(rng.integers(2)), int(rng.integers(2))
+        half_x, half_y = rng.random() < 0.2, rng.random() < 0.2
+        wx = 0.5 * d if half_x else d
+        wy = 0.5 * d if half_y else d
+        x0, x1 = (-wx, 0.0) if sx == 0 else (0.0, wx)
+        y0, y1 = (-wy, 0.0) if sy == 0 else (0.0, wy)
+        bx = 0.0 if half_x else (1.0 / d if sx == 0 else -1.0 / d)
+        by = 0.0 if half_y else (1.0 / d if sy == 0 else -1.0 / d)
+        cases.append((cx, cy, r, x0, x1, y0, y1, bx, by))
+    for _ in range(300):
+        r = float(rng.uniform(0.2, 5.0))
+        cx, cy = rng.uniform(-3, 3, 2)
+        x0, y0 = rng.uniform(-4, 3, 2)
+        x1, y1 = x0 + rng.uniform(0.01, 3), y0 + rng.uniform(0.01, 3)
+        cases.append((cx, cy, r, x0, x1, y0, y1, *rng.uniform(-2, 2, 2)))
+    # a circle tangent to a box line, and one through a corner
+    cases += [(0.0, -2.0, 2.0, -0.1, 0.1, 0.0, 0.1, 10.0, -10.0),
+              (-3.0, -4.0, 5.0, -0.1, 0.0, 0.0, 0.1, 10.0, -10.0)]
+    got = run([" ".join(["bil"] + [float(v).hex() for v in c]) for c in cases])
+    hits = 0
+    for c, g in zip(cases, got):
+        val = float.fromhex(g)
+        want = _bilinear_quadrature(*c)
+        scale = (c[4] - c[3]) + (c[6] - c[5])  # a bound on the arc length in the box
+        scale *= (1 + abs(c[7]) * max(abs(c[3]), abs(c[4]))) * \
+            (1 + abs(c[8]) * max(abs(c[5]), abs(c[6])))
+        assert abs(val - want) <= 1e-12 * scale, (c, val, want)
+        hits += want > 0
+    assert hits > 500
