@@ -186,3 +186,55 @@ def test_quarter_turn_and_mirror(orc):
     idx = (-np.arange(g.n_phi)) % g.n_phi
     np.testing.assert_allclose(orc.forward(g, np.ascontiguousarray(f[:, ::-1, :])), p[idx],
                                rtol=0, atol=1e-12 * np.max(p))
+
+
+def _gauss_srt(c, sig, s, ell):
+    """Continuous SRT (Sec. 2: the integral over the sphere of radius ell
+    about s) of exp(-|x - c|^2 / (2 sig^2)) in free space:
+    2 pi ell sig^2 / d (exp(-(d - ell)^2 / 2 sig^2) - exp(-(d + ell)^2 / 2 sig^2)),
+    d = |c - s|."""
+    d = float(np.linalg.norm(c - s))
+    return 2 * math.pi * ell * sig ** 2 / d * (np.exp(-(d - ell) ** 2 / (2 * sig ** 2))
+                                              - np.exp(-(d + ell) ** 2 / (2 * sig ** 2)))
+
+
+def test_linear_bases_approach_the_continuous_transform(orc):
+    """A Gaussian narrow enough to vanish at the volume's edge, sampled on
+    grids of 8^3 to 64^3 voxels (radius bins 3x the edge): every basis
+    approaches its closed-form SRT at about second order, and the bilinear
+    voxels with the linear intermediate are the closest at the finer levels
+    (measured 1.56x closer than both constant at 64^3)."""
+    R, L, sig = 6.0, 4.0, 0.45
+    c = np.array([0.31, -0.22, 0.17])
+    sub = 6
+    o = (np.arange(sub) + 0.5) / sub - 0.5
+    err = {}
+    for ms in (8, 16, 32, 64):
+        d = L / ms
+        xc = (np.arange(ms) - (ms - 1) / 2) * d
+        X, Y, Z = np.meshgrid(xc, xc, xc, indexing="ij")
+
+        def g(dx, dy, dz):
+            return np.exp(-((X + dx - c[0]) ** 2 + (Y + dy - c[1]) ** 2 + (Z + dz - c[2]) ** 2)
+                          / (2 * sig ** 2))
+        f_avg = sum(g(a * d, b * d, e * d) for a in o for b in o for e in o) / sub ** 3
+        f_node = sum(g(0.0, 0.0, e * d) for e in o) / sub  # values at the centres, slab means in z
+        n_ell, n_zs = 3 * ms, 4
+        g0 = orc.OracleGeometry.default(ms, ms, d, d, R, 16, n_zs, n_ell)
+        ell = g0.ell_lo + (np.arange(n_ell) + 0.5) * (g0.ell_hi - g0.ell_lo) / n_ell
+        zh = g0.zs_lo + (np.arange(n_zs) + 0.5) * (g0.zs_hi - g0.zs_lo) / n_zs
+        sh = np.array([[j, h, m] for j in (0, 3, 6) for h in range(n_zs) for m in range(n_ell)])
+        want = np.array([_gauss_srt(c, sig, np.array([R * math.cos(2 * math.pi * j / 16),
+                                                      R * math.sin(2 * math.pi * j / 16), zh[h]]),
+                                    ell[m]) for j, h, m in sh])
+        for vl in (False, True):
+            for rl in (False, True):
+                geo = orc.OracleGeometry.default(ms, ms, d, d, R, 16, n_zs, n_ell, rho_linear=rl,
+                                                 voxel_linear=vl)
+                p = orc.forward_shells(geo, f_node if vl else f_avg, sh)
+                err.setdefault((vl, rl), []).append(np.linalg.norm(p - want) / np.linalg.norm(want))
+    for key, e in err.items():
+        assert all(b < 0.4 * a for a, b in zip(e, e[1:])), (key, e)
+        assert e[-1] < 3e-3, (key, e)
+    assert err[(True, True)][-1] < 0.75 * err[(False, False)][-1], err
+    assert err[(True, True)][-2] < 0.75 * err[(False, False)][-2], err
