@@ -45,8 +45,8 @@ namespace {
 __device__ unsigned long long g_viol;  // gathered rows outside their operand
 #endif
 
-// Records gathered per step of the main loops (as in tiles.cu).
-constexpr int kU = 6;
+// Records per group of the main loop; two groups alternate, as in tiles.cu.
+constexpr int kH = 3;
 
 template <typename W>
 __device__ __forceinline__ void rec_w(const W* p, float w[4]);
@@ -151,31 +151,54 @@ __device__ __forceinline__ void a1t_pass(const A1Args& A, const W* __restrict__ 
     SRT_CHECK_GATHER(0, row, A.xrows, g_viol);
     return row;
   };
-  int e = e0;
-#pragma unroll 1
-  for (; e + kU <= e1; e += kU) {
-    int o[kU];
-    float wu[kU][4];
-    float4 v[kU][CH];
+  constexpr int H = kH;
+  int oA[H], oB[H];
+  float wA[H][4], wB[H][4];
+  float4 vA[H][CH], vB[H][CH];
+  // group of records eb .. eb + H - 1: gathered rows, then weights
+  auto load = [&](int eb, int (&o)[H], float (&w)[H][4], float4 (&v)[H][CH]) {
 #pragma unroll
-    for (int u = 0; u < kU; ++u) o[u] = row_of(__ldg(A.key + e + u));
+    for (int u = 0; u < H; ++u) o[u] = row_of(__ldg(A.key + eb + u));
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < H; ++u) {
       const float* xr = x0 + (int64_t)o[u] * ldx;
 #pragma unroll
       for (int c = 0; c < CH; ++c)
         if (in[c]) v[u][c] = srt_ldg_keep(xr + c * 128);
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u) rec_w<W>(wt + e + u, wu[u]);
+    for (int u = 0; u < H; ++u) rec_w<W>(wt + eb + u, w[u]);
+  };
+  auto comp = [&](float (&w)[H][4], float4 (&v)[H][CH]) {
 #pragma unroll
-    for (int u = 0; u < kU; ++u)
+    for (int u = 0; u < H; ++u)
 #pragma unroll
       for (int c = 0; c < CH; ++c)
         if (in[c]) {
 #pragma unroll
-          for (int sg = 0; sg < 4; ++sg) fma4(acc[sym_slot(PS, PM, sg)][c], wu[u][sg], v[u][c]);
+          for (int sg = 0; sg < 4; ++sg) fma4(acc[sym_slot(PS, PM, sg)][c], w[u][sg], v[u][c]);
         }
+  };
+  int e = e0;
+  const int groups = (e1 - e0) / H;
+  if (groups >= 2) {  // two groups alternate: one's gathers fly while the other computes
+    load(e, oA, wA, vA);
+    int gi = 1;
+#pragma unroll 1
+    for (; gi + 1 < groups; gi += 2) {
+      load(e + gi * H, oB, wB, vB);
+      comp(wA, vA);
+      load(e + (gi + 1) * H, oA, wA, vA);
+      comp(wB, vB);
+    }
+    if (gi < groups) {
+      load(e + gi * H, oB, wB, vB);
+      comp(wA, vA);
+      comp(wB, vB);
+    } else {
+      comp(wA, vA);
+    }
+    e += groups * H;
   }
 #pragma unroll 1
   for (; e < e1; ++e) {

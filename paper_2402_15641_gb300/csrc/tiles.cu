@@ -105,13 +105,15 @@ __device__ __forceinline__ void fma4(float2 (&a)[2], float w, const float4& xv) 
   a[1] = __ffma2_rn(ww, make_float2(xv.z, xv.w), a[1]);
 }
 
-// Records gathered per step of the main loop: all U gathered rows are
-// requested before the first of their FMAs, so a warp keeps U KB in flight.
-// The product waits on its gathers (L2 latency), and at 124 registers and 16
-// warps per SM six in flight per warp were fastest at 256^3 (A2 2.24 ms,
-// A2^T 2.06 ms; one record at a time, 60 registers and 32 warps: 2.77 /
-// 2.59 ms; L1 prefetch hints for later records instead: 3.5 / 3.3 ms).
-constexpr int kTileU = 6;
+// Records per group of the main loop.  The product waits on its gathers (L2
+// latency), so a warp alternates two groups: it requests the next group's
+// gathered rows before the FMAs of the current one, and its gathers stay in
+// flight while it computes.  At 128 registers and 16 warps per SM, groups
+// of three were fastest at 256^3 (A2 2.09 ms, A2^T 1.94 ms; a single group
+// of six whose FMAs wait for all its gathers: 2.24 / 2.06 ms; two groups
+// of two or of four: 3.20 / 3.29 and 3.60 / 4.20 ms; one record at a time,
+// 60 registers and 32 warps: 2.77 / 2.59 ms).
+constexpr int kTileH = 3;
 
 // Lanes own 4 consecutive dense columns of each of CH 128-column chunks.
 // TR: the block's outputs go through shared memory to the reshaped layout
@@ -139,35 +141,58 @@ __global__ void __launch_bounds__(256) k_tile22(TileArgs A, const W* __restrict_
     const int e0 = pp[0], e1 = pp[A.E];
     const int64_t xb = ADJ ? (int64_t)c * A.n_ell : (int64_t)c;
     const float* x0 = x + xb * ldx + n0;
-    constexpr int U = kTileU;
-    int e = e0;
-#pragma unroll 1
-    for (; e + U <= e1; e += U) {
-      int o[U];
-      float wu[U][4];
-      float4 v[U][CH];
+    constexpr int H = kTileH;
+    int oA[H], oB[H];
+    float wA[H][4], wB[H][4];
+    float4 vA[H][CH], vB[H][CH];
+    // group of records eb .. eb + H - 1: offsets, gathered rows, weights
+    auto load = [&](int eb, int (&o)[H], float (&w)[H][4], float4 (&v)[H][CH]) {
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        o[u] = __ldg(A.off + e + u);
+      for (int u = 0; u < H; ++u) {
+        o[u] = __ldg(A.off + eb + u);
         SRT_CHECK_GATHER(xb, o[u], A.xrows, g_viol);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
+      for (int u = 0; u < H; ++u) {
         const float* xr = x0 + (int64_t)o[u] * ldx;
 #pragma unroll
         for (int q = 0; q < CH; ++q)
           if (in[q]) v[u][q] = srt_ldg_keep(xr + q * 128);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) tile_w<W>(wt + e + u, wu[u]);
+      for (int u = 0; u < H; ++u) tile_w<W>(wt + eb + u, w[u]);
+    };
+    // its FMAs, record by record (the rows' summation order)
+    auto comp = [&](float (&w)[H][4], float4 (&v)[H][CH]) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+      for (int u = 0; u < H; ++u)
 #pragma unroll
         for (int q = 0; q < CH; ++q)
           if (in[q]) {
 #pragma unroll
-            for (int s = 0; s < 4; ++s) fma4(acc[s][q], wu[u][s], v[u][q]);
+            for (int s = 0; s < 4; ++s) fma4(acc[s][q], w[u][s], v[u][q]);
           }
+    };
+    int e = e0;
+    const int groups = (e1 - e0) / H;
+    if (groups >= 2) {
+      load(e, oA, wA, vA);
+      int gi = 1;
+#pragma unroll 1
+      for (; gi + 1 < groups; gi += 2) {
+        load(e + gi * H, oB, wB, vB);
+        comp(wA, vA);
+        load(e + (gi + 1) * H, oA, wA, vA);
+        comp(wB, vB);
+      }
+      if (gi < groups) {
+        load(e + gi * H, oB, wB, vB);
+        comp(wA, vA);
+        comp(wB, vB);
+      } else {
+        comp(wA, vA);
+      }
+      e += groups * H;
     }
 #pragma unroll 1
     for (; e < e1; ++e) {
