@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--rho-linear", action="store_true",
                    help="piecewise-linear intermediate in rho (else constant on the radius bins)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--e2e-steps", type=int, default=100)
     return p.parse_args()
 
 
