@@ -20,12 +20,12 @@ sys.path.insert(0, ROOT)
 from oracle import oracle as O  # noqa: E402
 from paper_2402_15641_gb300 import inputs as I  # noqa: E402
 
-CASES = [("srt16fd", False), ("srt16fd", True)]
+CASES = [("srt16fd", False, False), ("srt16fd", True, False), ("srt16fd", False, True)]
 
 
-def compute(name, rho_linear, n=48, seed=2024):
+def compute(name, rho_linear, voxel_linear=False, n=48, seed=2024):
     sz = I.sizes(name)
-    g = O.OracleGeometry.default(**sz, rho_linear=rho_linear)
+    g = O.OracleGeometry.default(**sz, rho_linear=rho_linear, voxel_linear=voxel_linear)
     f = I.phantom(name)
     y = I.probe(name)
     rng = np.random.default_rng(seed)
@@ -36,16 +36,18 @@ def compute(name, rho_linear, n=48, seed=2024):
     return sh, O.forward_shells(g, f, sh), vx, O.adjoint_voxels(g, y, vx)
 
 
-def path(name, rho_linear):
-    return os.path.join(HERE, f"oracle_{name}{'_rho_linear' if rho_linear else ''}.txt")
+def path(name, rho_linear, voxel_linear=False):
+    return os.path.join(HERE, f"oracle_{name}{'_rho_linear' if rho_linear else ''}"
+                              f"{'_voxel_linear' if voxel_linear else ''}.txt")
 
 
 def main():
-    for name, lin in CASES:
-        sh, p, vx, a = compute(name, lin)
-        with open(path(name, lin), "w") as fh:
+    for name, lin, vox in CASES:
+        sh, p, vx, a = compute(name, lin, vox)
+        with open(path(name, lin, vox), "w") as fh:
             fh.write(f"# FP64 oracle regression values, workload {name}, intermediate "
-                     f"{'piecewise linear in rho' if lin else 'piecewise constant'}; written by\n"
+                     f"{'piecewise linear in rho' if lin else 'piecewise constant'}"
+                     f"{', voxels bilinear between centres' if vox else ''}; written by\n"
                      "# tests/golden/make_golden.py (oracle/ only; the paper prints no worked example)\n")
             fh.write("# kind i0 i1 i2 value: fwd = p[j][h][m] of the seeded phantom; "
                      "adj = (A^T g)[ix][iy][k] of the seeded probe\n")
