@@ -88,3 +88,19 @@ def test_traffic_reported_only_for_the_sources_it_was_taken_on(tmp_path, monkeyp
         fh.write("\n// edited\n")
     assert bench.csrc_digest() != digest
     assert bench.ncu_traffic("fwd.spmm2", "w") is None
+
+
+@pytest.mark.parametrize("extra", [[], ["--rho-linear", "--voxel-linear"], ["--weights", "bf16"]])
+def test_reference_arm_runs_on_cpu(extra):
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) on the
+    16^3 workload prints its one JSON line, with every option of the CUDA
+    arm accepted."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "srt16fd", "--steps", "1", "--warmup", "0", *extra],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
