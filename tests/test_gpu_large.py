@@ -111,3 +111,35 @@ def test_srt256_bf16_against_fp32(srt, orc, srt256_inputs):
     print(f"PARITY srt256 bf16 vs fp32 entries (full output): forward rel-L2 {e_p:.3e}, "
           f"adjoint rel-L2 {e_a:.3e}")
     assert 1e-5 < e_p <= 5e-3 and 1e-5 < e_a <= 5e-3
+
+
+def test_srt512_sampled_maximum_size(srt, orc):
+    """The largest workload the suite runs: 512^3 voxels at 0.05 mm, 256
+    sensor columns, 512 rings, 1536 radius bins (8x the benchmark's voxels,
+    about 4 GB on the device), in the default form (8-fold A1, Toeplitz taps,
+    register tiles).  Every index the kernels form (tile-record offsets,
+    A1^T keys j << 16 | l, pixel indices under the multiply-shift quotient of
+    the symmetry map, row offsets into 805 MB operands) is larger here than
+    anywhere else; sampled shells and voxels against the oracle, on a volume
+    that is random inside the central 48^3 voxels and zero elsewhere, and
+    the adjoint identity over the whole output."""
+    sz = dict(ms=512, mz=512, dxy=0.05, dz=0.05, radius=20.0, n_phi=256, n_zs=512, n_ell=1536)
+    g, o = geom_pair(orc, **sz)
+    plan = srt.Plan(g)
+    assert plan.info["a1_rot"] == 2 and plan.info["a2_taps"] == 1
+    assert min(plan.info["tile_records"]) > 0
+    rng = np.random.default_rng(51)
+    c = 48
+    a = (g.ms - c) // 2
+    f = np.zeros(g.f_shape, dtype=np.float32)
+    f[a:a + c, a:a + c, a:a + c] = rng.uniform(0, 1, (c, c, c))
+    y = rng.standard_normal(g.p_shape, dtype=np.float32)
+    sh, vx = _samples(g, 512, 24, 52, crop=c)
+    e_p, e_a = _check(srt, orc, plan, o, f, y, sh, vx, 1e-5)
+    print(f"PARITY srt512 fp32 (48^3 crop, 512 shells, 24 voxels): forward rel-L2 {e_p:.3e}, "
+          f"adjoint rel-L2 {e_a:.3e}")
+    fd, yd = to_dev(f), to_dev(y)
+    af, aty = plan.forward(fd), plan.adjoint(yd)
+    lhs, rhs = srt.dot_f64(af, yd), srt.dot_f64(fd, aty)
+    assert abs(lhs - rhs) / math.sqrt(srt.dot_f64(af, af) * srt.dot_f64(yd, yd)) <= 1e-6
+    plan.close()
