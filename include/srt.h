@@ -157,7 +157,10 @@ typedef struct srt_plan_info_t {
                               /*    stored, the rest follow by quarter turns; */
                               /* 2: the first n_phi/8 + 1, by quarter turns   */
                               /*    and the diagonal mirror; 0: every column  */
-  int32_t reserved;
+  int32_t tile_order;         /* bit 0: A2's register tiles are issued from   */
+                              /* the last radius pair down, bit 1: A2^T's     */
+                              /* (the end of the radius range whose tiles     */
+                              /* hold more records goes first); 0 otherwise   */
   int64_t tile_records[3];    /* records of the register-tile products: A2,   */
                               /* A2^T (2 x 2 row tiles) and A1^T (2 x 2 pixel */
                               /* tiles); 0 where that product runs row-wise   */

@@ -44,7 +44,7 @@ class SrtPlanInfo(ctypes.Structure):
         ("dropped1", ctypes.c_int64), ("dropped2", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64), ("weight_dtype", ctypes.c_int32),
         ("a2_taps", ctypes.c_int32), ("n_taps", ctypes.c_int64),
-        ("a1_rot", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("a1_rot", ctypes.c_int32), ("tile_order", ctypes.c_int32),
         ("tile_records", ctypes.c_int64 * 3),
     ]
 

@@ -436,7 +436,7 @@ int srt_plan_info(srt_plan_t p, srt_plan_info_t* o) {
   o->a2_taps = p->toeplitz;
   o->n_taps = p->toeplitz ? p->tm.nnz : 0;
   o->a1_rot = p->a1_rot;
-  o->reserved = 0;
+  o->tile_order = (p->tiles && p->tlf.desc ? 1 : 0) | (p->tiles && p->tla.desc ? 2 : 0);
   o->tile_records[0] = p->tiles ? p->tlf.nrec : 0;
   o->tile_records[1] = p->tiles ? p->tla.nrec : 0;
   o->tile_records[2] = p->a1tiles ? p->a1tl.na : 0;

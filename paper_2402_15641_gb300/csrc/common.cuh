@@ -93,6 +93,7 @@ struct SrtTaps {
 // offset from the tile) with the first record of each key in ptr.
 struct SrtTiles {
   int pairs = 0, nkeys = 0, key0 = 0;
+  bool desc = false;       // blocks issued from the last radius pair down
   int64_t nrec = 0;
   int32_t* ptr = nullptr;  // pairs * (nkeys + 1)
   int32_t* off = nullptr;  // nrec

@@ -61,6 +61,7 @@ struct TileArgs {
   int c0, c1;          // tile coordinate range (forward: rings, adjoint: slabs)
   int n_ell, mz;
   int G, R, TG;        // block order: G coordinate pairs x R radius pairs
+  int desc;            // radius chunks issued from the last one down
   int xrows;           // rows of the gathered operand (debug-build checks)
   int64_t ldn;         // fused reshape: stride of the output's columns n
 };
@@ -84,14 +85,25 @@ __device__ __forceinline__ void tile_w<uint2>(const uint2* p, float w[4]) {
   w[3] = __uint_as_float(v.y & 0xffff0000u);
 }
 
-// Tile of this warp: a block owns TG coordinate pairs x 8/TG radius pairs,
-// blocks issued radius-chunk-major (all coordinate pairs advance through the
-// radius chunks together, so the rows gathered at any time stay in L2).
+// Radius chunk ch and coordinate tile t of this block.  Blocks are issued
+// radius-chunk-major (all coordinate pairs advance through the radius
+// chunks together, so the rows gathered at any time stay in L2), from the
+// end of the radius range whose chunks hold more records: the last blocks
+// to start are then the light ones, and the SMs finish together.
+__device__ __forceinline__ void block_chunk(const TileArgs& A, int TG, int* ch, int* t) {
+  const int TI = 8 / TG;
+  const int tiles = (A.G + TG - 1) / TG;
+  const int c = blockIdx.x / tiles;
+  *t = blockIdx.x - c * tiles;
+  *ch = A.desc ? (A.R + TI - 1) / TI - 1 - c : c;
+}
+
+// Tile of this warp: a block owns TG coordinate pairs x 8/TG radius pairs.
 __device__ __forceinline__ bool tile_of(const TileArgs& A, int* g, int* r) {
   const int w = threadIdx.x >> 5;
   const int TI = 8 / A.TG;
-  const int tiles = (A.G + A.TG - 1) / A.TG;
-  const int ch = blockIdx.x / tiles, t = blockIdx.x - ch * tiles;
+  int ch, t;
+  block_chunk(A, A.TG, &ch, &t);
   *g = t * A.TG + w / TI;
   *r = ch * TI + w % TI;
   return *g < A.G && *r < A.R;
@@ -233,8 +245,8 @@ __global__ void __launch_bounds__(256) k_tile22(TileArgs A, const W* __restrict_
   // coordinate 0..7 (ring or slab), rl = its radius 0..3 (radius or bin)
   __shared__ __align__(16) float S[8 * 4 * 64];
   const int w = threadIdx.x >> 5;
-  const int tiles = (A.G + 3) / 4;
-  const int ch = blockIdx.x / tiles, t = blockIdx.x - ch * tiles;
+  int ch, t;
+  block_chunk(A, 4, &ch, &t);
   const int cb = A.c0 + 8 * t, rb = 4 * ch;  // the block's first coordinate and radius
 #pragma unroll
   for (int pass = 0; pass < 2 * CH; ++pass) {
@@ -367,6 +379,21 @@ int build_dir(const srt_plan_s* plan, bool adj, const std::vector<int32_t>& rp,
     while (next_key <= nkeys) pk[next_key++] = (int32_t)off.size();
   }
   if (off.size() >= ((size_t)1 << 31)) return SRT_ERR_GEOMETRY;
+  // Issue order: the heavier end of the radius range first (a tile's time
+  // follows its record count; the forward's records grow with the radius
+  // until the semicircle reaches the largest ring-to-slab offset, the
+  // adjoint's fall from the first radius bins on).  Compared over the first
+  // and last eighth of the radius pairs.
+  {
+    const int e = std::max(1, pairs / 8);
+    int64_t lo = 0, hi = 0;
+    for (int p = 0; p < e; ++p) {
+      lo += ptr[(int64_t)p * (nkeys + 1) + nkeys] - ptr[(int64_t)p * (nkeys + 1)];
+      const int q = pairs - 1 - p;
+      hi += ptr[(int64_t)q * (nkeys + 1) + nkeys] - ptr[(int64_t)q * (nkeys + 1)];
+    }
+    t->desc = hi > lo;
+  }
   t->pairs = pairs;
   t->nkeys = nkeys;
   t->key0 = key0;
@@ -415,7 +442,7 @@ int srt_tiles_apply(const srt_plan_s* plan, bool adjoint, int c0, int c1, int TG
   if (TG != 1 && TG != 2 && TG != 4 && TG != 8) TG = 4;
   if (ldn > 0) TG = 4;  // the fused reshape stages blocks of 8 x 4 output rows
   TileArgs A{t.ptr, t.off, t.nkeys, t.key0, adjoint ? g.n_zs : g.mz, c0, c1, g.n_ell, g.mz,
-             (c1 - c0 + 1) / 2, t.pairs, TG,
+             (c1 - c0 + 1) / 2, t.pairs, TG, t.desc ? 1 : 0,
              srt_checked_rows(adjoint ? (int64_t)g.n_zs * g.n_ell : (int64_t)g.n_ell * g.mz),
              ldn};
   if (g.weight_dtype == SRT_BF16) {

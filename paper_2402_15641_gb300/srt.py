@@ -133,7 +133,7 @@ class Plan:
         self._ws = {}
         info = L.SrtPlanInfo()
         check(self._lib.srt_plan_info(self._h, ctypes.byref(info)), "srt_plan_info")
-        self.info = {k: getattr(info, k) for k, _ in L.SrtPlanInfo._fields_ if k != "reserved"}
+        self.info = {k: getattr(info, k) for k, _ in L.SrtPlanInfo._fields_}
         self.info["tile_records"] = list(info.tile_records)
 
     # -------------------------------------------------------------- memory

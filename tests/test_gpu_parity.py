@@ -560,3 +560,53 @@ def test_tiles_equal_rowwise_taps(srt, orc, sz, wdt, batch):
     tol = FP32_TOL if wdt == "fp32" else BF16_TOL
     assert rel_l2(to_np(plan.forward(f)[0]), orc.forward(o, to_np(f)[0])) <= tol
     assert rel_l2(to_np(plan.adjoint(y)[-1]), orc.adjoint(o, to_np(y)[-1])) <= tol
+
+
+def _pair_records(orc, sz):
+    """Records per radius pair of the 2 x 2 tiles of A2 (pairs of radii m)
+    and A2^T (pairs of radius bins l), counted from the oracle's semicircle
+    cells.  With the rings at the slab centres, T's taps are one ring's
+    semicircle cells at every ring-to-slab offset d, which the middle ring
+    of a volume 2 mz - 1 slabs tall sees.  A forward record is a distinct
+    (l, d + i) and an adjoint record a distinct (i - d, m), i = 0, 1 the
+    tile's two rings or slabs."""
+    _, tall = geom_pair(orc, **dict(sz, mz=2 * sz["mz"] - 1, n_zs=2 * sz["n_zs"] - 1))
+    h, n = sz["n_zs"] - 1, sz["n_ell"]
+    cells = [{(c // tall.mz, c % tall.mz - h) for c, w in orc.semicircle_arcs(tall, h, m).items()
+              if w != 0.0} for m in range(n)]
+    by_l = {}
+    for m, cs in enumerate(cells):
+        for l, d in cs:
+            by_l.setdefault(l, []).append((m, d))
+    fwd, adj = [], []
+    for p in range(0, n, 2):
+        two = [q for q in (p, p + 1) if q < n]
+        fwd.append(len({(l, d + i) for m in two for l, d in cells[m] for i in (0, 1)}))
+        adj.append(len({(i - d, m) for l in two for m, d in by_l.get(l, ()) for i in (0, 1)}))
+    return fwd, adj
+
+
+@pytest.mark.parametrize("name", ["srt16fd", "srt32", "srt128"])
+def test_tile_records_and_block_order(srt, orc, name):
+    """The plan's tile records are the distinct (offset, row) pairs of T's
+    taps per radius pair, and its blocks start at the end of the radius range
+    whose first or last eighth of the pairs holds more records: A2's records
+    grow with the radius up to the largest ring-to-slab offset, so its
+    blocks run from the last radius pair down (bit 0 of tile_order); A2^T's
+    fall from the first radius bins, so its blocks run upwards (bit 1
+    clear).  test_tiles_equal_rowwise_taps checks the results in that order
+    (srt32, srt16fd) bitwise."""
+    sz = dict(I.sizes(name))
+    g, _ = geom_pair(orc, **sz)
+    info = srt.Plan(g).info
+    fwd, adj = _pair_records(orc, sz)
+    assert info["tile_records"][:2] == [sum(fwd), sum(adj)]
+
+    def heavier_last(r):
+        e = max(1, len(r) // 8)
+        return sum(r[-e:]) > sum(r[:e])
+
+    assert info["tile_order"] == (1 if heavier_last(fwd) else 0) | (2 if heavier_last(adj) else 0)
+    assert info["tile_order"] == 1
+    gr, _ = geom_pair(orc, rowwise=True, **sz)
+    assert srt.Plan(gr).info["tile_order"] == 0
