@@ -166,10 +166,11 @@ def ncu_traffic(kernel_stage, workload):
     return float(v) if v else None
 
 
-def stage_model(geom, info, batch, weights, fused=False):
+def stage_model(geom, info, batch, weights, fused=False, fused_p1=False):
     """Algorithmic FLOPs and compulsory bytes per launch of each stage.
     fused: A2 writes p and A2^T writes F1 in the reshaped layouts (no P2 and
-    P1^-1 kernels; their stages are dropped, the products' bytes unchanged)."""
+    P1^-1 kernels); fused_p1: A1 writes Y1' (no P1 kernel).  The fused
+    reshapes' stages are dropped, the products' bytes unchanged."""
     vb = 2 if weights == "bf16" else 4
     pix, c1 = geom.ms * geom.ms, geom.n_ell * geom.mz
     r1, r2 = geom.n_phi * geom.n_ell, geom.n_zs * geom.n_ell
@@ -206,12 +207,10 @@ def stage_model(geom, info, batch, weights, fused=False):
     spmm1["fma_per_gather"] = 1.0
     p1 = dict(flop=0, bytes=2 * y1)
     p2 = dict(flop=0, bytes=2 * pp)
-    if fused:
-        return {"fwd": [("spmm1", spmm1), ("permute1", p1), ("spmm2", spmm2), None],
-                "adj": [("permute2_inv", p2), ("spmm2t", spmm2t), None, ("spmm1t", spmm1t)]}
-    return {"fwd": [("spmm1", spmm1), ("permute1", p1), ("spmm2", spmm2), ("permute2", p2)],
-            "adj": [("permute2_inv", p2), ("spmm2t", spmm2t), ("permute1_inv", p1),
-                    ("spmm1t", spmm1t)]}
+    return {"fwd": [("spmm1", spmm1), None if fused_p1 else ("permute1", p1), ("spmm2", spmm2),
+                    None if fused else ("permute2", p2)],
+            "adj": [("permute2_inv", p2), ("spmm2t", spmm2t),
+                    None if fused else ("permute1_inv", p1), ("spmm1t", spmm1t)]}
 
 
 def dist_init():
@@ -418,8 +417,11 @@ def run_ours(args):
     value = job_rate(world, args.steps, B, total_ms)
 
     # per-stage figures from the CUDA events recorded on the launch stream
-    fused = plan.launches_per_call(0, B) == 3
-    model = stage_model(geom, plan.info, B, args.weights, fused)
+    # reshapes fused into the products: the tile products' (P2, P1^-1) take
+    # one launch off each direction, A1's (P1) one more off the forward
+    n_fwd, n_adj = plan.launches_per_call(0, B), plan.launches_per_call(1, B)
+    fused, fused_p1 = n_adj == 3, n_fwd == n_adj - 1
+    model = stage_model(geom, plan.info, B, args.weights, fused, fused_p1)
     stages = {}
     for d in ("fwd", "adj"):
         mean = np.mean(np.array(stage[d]), axis=0)
@@ -545,9 +547,11 @@ def run_ours(args):
                                                   + ("; a warp per row" if args.rowwise
                                                      else "; A1 a warp per row, A1^T 2 x 2-pixel "
                                                           "register tiles"),
-                                      "reshapes": ("P2 and P1^-1 fused into the A2 / A2^T "
-                                                   "epilogues" if fused else
-                                                   "four reshape kernels"),
+                                      "reshapes": ", ".join(
+                                          (["P1 fused into the A1 epilogue"] if fused_p1 else [])
+                                          + (["P2 and P1^-1 fused into the A2 / A2^T epilogues"]
+                                             if fused else []))
+                                      or "four reshape kernels",
                                       "plan_device_gb": round(plan.info["device_bytes"] / 1e9, 3),
                                       "intermediate": ("piecewise linear in rho" if args.rho_linear
                                                        else "piecewise constant on radius bins"),

@@ -77,15 +77,19 @@ enum srt_weight_dtype { SRT_FP32 = 0, SRT_BF16 = 1 };
  * n_phi/4 under quarter turns (n_phi % 4 == 0, the whole aperture), else
  * every column. */
 #define SRT_A1_FULL 0x40
-/* SRT_FUSE_RESHAPES: fold the reshapes P2 (forward) and P1^-1 (adjoint) into
- * the products before them.  When A2 and A2^T are applied from register
- * tiles (srt_plan_info_t.tile_records[0] > 0) and the dense width
- * batch * n_phi is a multiple of 4, those products then write their output
- * straight into the reshaped layout (p[b][j][h][m]; F1[b][j][l][k]) and a
- * call makes 3 kernel launches instead of 4; the results are bitwise the
- * same.  Off by default: the reshaped layouts take each dense column as a
- * separate 16- or 32-byte piece, which costs the products more than the
- * separate reshape kernels (which run at HBM speed) cost. */
+/* SRT_FUSE_RESHAPES: fold the reshapes P1, P2 (forward) and P1^-1 (adjoint)
+ * into the products before them.  When A2 and A2^T are applied from
+ * register tiles (srt_plan_info_t.tile_records[0] > 0) and the dense width
+ * batch * n_phi is a multiple of 4, those products write their output
+ * straight into the reshaped layout (p[b][j][h][m]; F1[b][j][l][k]); when
+ * A1 is stored for a fundamental set of columns (srt_plan_info_t.a1_rot >
+ * 0) and n_phi and mz are multiples of 4, the A1 product writes Y1' (rows
+ * (l, k), columns b * n_phi + j) itself.  A forward call then makes 2 or 3
+ * kernel launches instead of 4, an adjoint 3 (srt_launches_per_call); the
+ * results are bitwise the same.  Off by default: the reshaped layouts take
+ * each dense column as a separate 16- or 32-byte piece, which costs the
+ * products more than the separate reshape kernels (which run at HBM speed)
+ * cost. */
 #define SRT_FUSE_RESHAPES 0x80
 /* SRT_VOXEL_LINEAR: the volume is piecewise linear in x and y instead of
  * constant on the voxels (Sec. 3.1 notes the method carries over to other
@@ -363,15 +367,17 @@ int srt_plan_export(srt_plan_t plan, int32_t which, int32_t* rowptr, int32_t* co
  * then returns, for the LAST call in direction dir (0 forward, 1 adjoint), the
  * elapsed milliseconds of its stages in launch order (n >= 4: first SpMM,
  * permute, second SpMM, permute) after synchronising on the last event.
- * With the fused reshapes (SRT_FUSE_RESHAPES) the fused permute's
- * stage reads 0 and its time is part of the product before (forward) or
- * after (adjoint) it.
+ * With the fused reshapes (SRT_FUSE_RESHAPES) a fused permute's stage
+ * reads 0 and its time is part of the product before it (A1 for P1, A2 for
+ * P2, A2^T for P1^-1).
  * Not for use with stream capture.  Errors: SRT_ERR_ARG, SRT_ERR_NOT_READY.
  */
 int srt_plan_set_timing(srt_plan_t plan, int32_t enable);
 int srt_stage_times(srt_plan_t plan, int32_t dir, float* ms, int32_t n);
 
-/* Number of kernel launches one srt_forward / srt_adjoint call makes. */
+/* Number of kernel launches one srt_forward (dir 0) or srt_adjoint (dir 1)
+ * call on `batch` volumes makes: 4 (two products, two reshapes), fewer with
+ * SRT_FUSE_RESHAPES.  0 for a null plan, batch <= 0 or another dir. */
 int srt_launches_per_call(srt_plan_t plan, int32_t dir, int32_t batch);
 
 /*

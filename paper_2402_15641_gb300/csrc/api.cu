@@ -190,9 +190,15 @@ int sink_copy(HostSink* hs, int chunk, cudaStream_t st, float* host, const float
 // reshape run in kHostChunks ring ranges and each range of p is copied to
 // the host while the next one is computed (no per-stage timing then).
 // With SRT_FUSE_RESHAPES the tile products write their output in the layout
-// of the step after the reshape (P2 in the forward, P1^-1 in the adjoint).
+// of the step after the reshape (P2 in the forward, P1^-1 in the adjoint),
+// and so does the A1 product stored by rotation (P1: blocks of 4 sensor
+// columns x 2 radii, 16-byte pieces of 4 columns).
 bool fused_reshapes(const srt_plan_s* p, int64_t nb) {
   return p->tiles && nb % 4 == 0 && (p->g.flags & SRT_FUSE_RESHAPES);
+}
+bool fused_p1(const srt_plan_s* p) {
+  return p->a1_rot && p->g.n_phi % 4 == 0 && p->g.mz % 4 == 0 &&
+         (p->g.flags & SRT_FUSE_RESHAPES);
 }
 
 int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, float* w1,
@@ -206,18 +212,22 @@ int run_forward(srt_plan_s* p, const float* f, float* out, int B, float* w0, flo
   // Y1[b][j][l][k] = A1 F_b (CRT in the first plane, all slabs at once)
   // rows (j, l) visited radius-chunk-major across sensor columns (L2 reuse of F)
   {
-    NvRange r("A1 product");
+    NvRange r(fused_p1(p) ? "A1 product + reshape P1" : "A1 product");
     // CSR rows, a warp per row: the 8 warps of a block take 8 consecutive
     // radii of one column, whose circles cross the same pixels, and share
     // those gathers in L1 (46% hits).  4-radius register tiles
     // (srt_a1tiles_apply) fetch each pixel once per tile instead, but lose
     // that sharing (13% L1 hits) and measured slower (1.74-1.97 against
     // 1.56 ms at 256^3).
-    SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz, B,
-                     st, g.n_phi, g.n_ell, 1, 0, r1, a1_rot(p, 1)));
+    if (fused_p1(p))  // writing Y1' (the reshape P1's output) itself
+      SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w1, 0, 0, g.mz, B, st,
+                       g.n_phi, g.n_ell, 4, 0, r1, a1_rot(p, 1), 0, nb));
+    else
+      SRT_TRY(srt_spmm(p->a1, g.weight_dtype, f, g.mz, pix * g.mz, w0, g.mz, r1 * g.mz, g.mz,
+                       B, st, g.n_phi, g.n_ell, 1, 0, r1, a1_rot(p, 1)));
   }
   if (!hs) mark(p, 0, 1, st);
-  {
+  if (!fused_p1(p)) {
     NvRange r("reshape P1");
     SRT_TRY(srt_transpose(w0, c1, (int64_t)g.n_phi * c1, w1, nb, g.n_phi, g.n_phi, (int)c1, B, st));
   }
@@ -884,9 +894,9 @@ int srt_stage_times(srt_plan_t p, int32_t dir, float* ms, int32_t n) {
 }
 
 int srt_launches_per_call(srt_plan_t p, int32_t dir, int32_t batch) {
-  (void)dir;
-  if (!p || batch <= 0) return 0;
-  return fused_reshapes(p, (int64_t)batch * p->g.n_phi) ? 3 : 4;
+  if (!p || batch <= 0 || dir < 0 || dir > 1) return 0;
+  return 4 - (fused_reshapes(p, (int64_t)batch * p->g.n_phi) ? 1 : 0) -
+         (dir == 0 && fused_p1(p) ? 1 : 0);
 }
 
 int srt_plan_destroy(srt_plan_t p) {

@@ -201,11 +201,13 @@ struct SrtRot {
 // launch's rows (G groups of R) are visited chunk-major across groups, a
 // block owning TG groups (1, 2, 4 or 8) x 8/TG consecutive rows of each.
 // With S > 0 (dividing G and R) the blocks walk S x S super-tiles of the
-// G x R row grid instead of chunk-major bands.
+// G x R row grid instead of chunk-major bands.  ldn > 0 (A1 with rot.mode
+// 1, G = n_phi, R = n_ell, ncols = mz, batch items b): y is Y1', the
+// output of the reshape P1, y[(l ncols + k) ldn + b G + j] for row (j, l).
 int srt_spmm(const SrtCsr& A, int weight_dtype, const float* x, int64_t ldx, int64_t bsx, float* y,
              int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t stream, int G = 0,
              int R = 0, int TG = 1, int64_t r0 = 0, int64_t rows = -1, SrtRot rot = SrtRot(),
-             int S = 0);
+             int S = 0, int64_t ldn = 0);
 
 // out[b*obs + c*old + r] = in[b*ibs + r*ild + c] for r < rows, c < cols.
 int srt_transpose(const float* in, int64_t ild, int64_t ibs, float* out, int64_t old, int64_t obs,

@@ -94,6 +94,7 @@ struct Rows {
   SrtRot rot;
   uint64_t magic;  // ceil(2^40 / rot.ms)
   int xrows;       // rows of the gathered operand (debug-build checks)
+  int64_t ldn;     // > 0: reshape P1 fused (k_spmm_rot), stride of Y1''s rows
 };
 
 // Stored row and gathered-row remap of segment s of output row `row`.
@@ -185,7 +186,11 @@ __global__ void __launch_bounds__(256) k_spmm_plain(int rows, const int32_t* __r
 // (j, l) of A1 from stored row (j mod q, l), pixels turned j / q times.
 // MODE 2: row p of A1^T from stored rows rot^-s(p), s = 0..3, gathered rows
 // shifted by s q n_ell.  rowptr: the stored matrix's own pointers.
-template <typename V, int CH, int MODE>
+// TR (MODE 1, blocks of 4 sensor columns x 2 radii, G = n_phi, R = n_ell):
+// the reshape P1 in the epilogue.  The block's 8 rows go through shared
+// memory, 128 slabs at a time, and are written as Y1'[(l, k)][b G + j],
+// row stride ldn, 16 bytes (4 sensor columns) per radius and slab.
+template <typename V, int CH, int MODE, bool TR>
 __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
                                                   const int32_t* __restrict__ rowptr,
                                                   const int32_t* __restrict__ col,
@@ -194,13 +199,15 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
                                                   int64_t bsx, float* __restrict__ y, int64_t ldy,
                                                   int64_t bsy, int ncols, int G, int R, int TG,
                                                   int S, int ms, int n_ell, int q,
-                                                  int mirror, uint64_t magic, int xrows) {
+                                                  int mirror, uint64_t magic, int xrows,
+                                                  int64_t ldn) {
   const int lane = threadIdx.x & 31;
   const int lr = block_row(G, R, TG, S);
-  if (lr < 0 || lr >= rows) return;
-  const int row = r0 + lr;
+  const bool mine = lr >= 0 && lr < rows;
+  if (!TR && !mine) return;  // (TR: every warp reaches the block barrier)
+  const int row = r0 + (mine ? lr : 0);
   x += blockIdx.z * bsx;
-  y += blockIdx.z * bsy;
+  if (!TR) y += blockIdx.z * bsy;
   const int n0 = blockIdx.y * (128 * CH) + lane * 4;
   float4 acc[CH];
 #pragma unroll
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
   for (int s = 0; s < (MODE == 2 ? 4 : 1); ++s) {
     if (MODE == 2) sr = rot_pixel(row, 4 - s, ms, magic);
     const int off = MODE == 2 ? s * q * n_ell : 0;
-    const int e0 = rowptr[sr], e1 = rowptr[sr + 1];
+    const int e0 = rowptr[sr], e1 = TR && !mine ? e0 : rowptr[sr + 1];
     for (int eb = e0; eb < e1; eb += 32) {
       int c = 0;
       float v = 0.f;
@@ -251,11 +258,34 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
       }
     }
   }
-  float* yr = y + (int64_t)lr * ldy;
+  if (!TR) {
+    float* yr = y + (int64_t)lr * ldy;
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {
+      const int n = n0 + k * 128;
+      if (n < ncols) *reinterpret_cast<float4*>(yr + n) = acc[k];
+    }
+    return;
+  }
+  // fused P1: Sb[w][n] holds row w = 2 jl + il (column j0 + jl, radius
+  // l0 + il) of the block, 128 slabs n; a thread then writes one radius and
+  // slab of the 4 columns
+  __shared__ __align__(16) float Sb[8 * 128];
+  const int w = threadIdx.x >> 5, tiles = (G + 3) / 4;
+  const int c = blockIdx.x / tiles, tt = blockIdx.x - c * tiles;
+  const int il = threadIdx.x >> 7, nl = threadIdx.x & 127;
+  const int l = 2 * c + il;
+  const int64_t cb = (int64_t)blockIdx.z * G + 4 * tt;  // column b G + j0 of Y1'
 #pragma unroll
   for (int k = 0; k < CH; ++k) {
-    const int n = n0 + k * 128;
-    if (n < ncols) *reinterpret_cast<float4*>(yr + n) = acc[k];
+    if (k) __syncthreads();  // the previous chunk's reads are done
+    *reinterpret_cast<float4*>(Sb + w * 128 + lane * 4) = acc[k];
+    __syncthreads();
+    const int n = blockIdx.y * (128 * CH) + k * 128 + nl;
+    if (l < R && n < ncols && 4 * tt < G)
+      *reinterpret_cast<float4*>(y + ((int64_t)l * ncols + n) * ldn + cb) =
+          make_float4(Sb[il * 128 + nl], Sb[(2 + il) * 128 + nl], Sb[(4 + il) * 128 + nl],
+                      Sb[(6 + il) * 128 + nl]);
   }
 }
 
@@ -340,13 +370,19 @@ int launch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t
     const int CH = chunks >= 2 ? 2 : chunks;
     dim3 grid(gx, (ncols + 128 * CH - 1) / (128 * CH), batch);
     const SrtRot& r = W.rot;
-#define SRT_ROT_LAUNCH(C)                                                                     \
-  k_spmm_rot<V, C, MODE><<<grid, block, 0, st>>>(W.rows, W.r0, A.rowptr, A.col, val, x, ldx, \
-                                                 bsx, y, ldy, bsy, ncols, W.G, W.R, W.TG,    \
-                                                 W.S, r.ms, r.n_ell, r.q, r.mirror, W.magic, \
-                                                 W.xrows)
-    if (CH == 2) SRT_ROT_LAUNCH(2);
-    else SRT_ROT_LAUNCH(1);
+#define SRT_ROT_LAUNCH(C, T)                                                                  \
+  k_spmm_rot<V, C, MODE, T><<<grid, block, 0, st>>>(W.rows, W.r0, A.rowptr, A.col, val, x,   \
+                                                    ldx, bsx, y, ldy, bsy, ncols, W.G, W.R,   \
+                                                    W.TG, W.S, r.ms, r.n_ell, r.q, r.mirror,  \
+                                                    W.magic, W.xrows, W.ldn)
+    if (MODE == 1 && W.ldn > 0) {
+      if (CH == 2) SRT_ROT_LAUNCH(2, MODE == 1);
+      else SRT_ROT_LAUNCH(1, MODE == 1);
+    } else if (CH == 2) {
+      SRT_ROT_LAUNCH(2, false);
+    } else {
+      SRT_ROT_LAUNCH(1, false);
+    }
 #undef SRT_ROT_LAUNCH
   } else {
     dim3 grid((W.rows + 7) / 8, (ncols + 127) / 128, batch);
@@ -372,7 +408,7 @@ int dispatch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64
 
 int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx, float* y,
              int64_t ldy, int64_t bsy, int ncols, int batch, cudaStream_t st, int G, int R,
-             int TG, int64_t r0, int64_t rows, SrtRot rot, int S) {
+             int TG, int64_t r0, int64_t rows, SrtRot rot, int S, int64_t ldn) {
   if (rows < 0) rows = A.rows - r0;
   if (rows <= 0) return SRT_OK;
   if (rows > 0x7fffffff || r0 + rows > 0x7fffffff) return SRT_ERR_ARG;
@@ -389,7 +425,16 @@ int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx,
   // gathered operand: A's columns, or for A1^T from the stored quarter
   // (mode 2) the rows (j, l) of every sensor column
   const int64_t xr = rot.mode == 2 ? (int64_t)4 * rot.q * rot.n_ell : A.cols;
-  const Rows W{(int)rows, (int)r0, G, R, TG, S, rot, magic, srt_checked_rows(xr)};
+  if (ldn > 0) {
+    // fused P1: the rotated-rows kernel with blocks of 4 sensor columns x
+    // 2 radii over all rows, 16-byte aligned pieces of Y1'
+    if (rot.mode != 1 || G <= 0 || r0 != 0 || G % 4 || ncols % 4 || ldx % 4 || bsx % 4 ||
+        ldn % 4 || (uintptr_t)x % 16 || (uintptr_t)y % 16 || (int64_t)batch * G > ldn)
+      return SRT_ERR_ARG;
+    TG = 4;
+    S = 0;
+  }
+  const Rows W{(int)rows, (int)r0, G, R, TG, S, rot, magic, srt_checked_rows(xr), ldn};
   if (wdt == SRT_BF16) return dispatch<uint16_t>(A, A.v16, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
   return dispatch<float>(A, A.v32, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
 }

@@ -72,3 +72,16 @@ def test_fused_reshapes_model():
         for a, b in zip(fused[d], plain[d]):
             if a is not None:
                 assert a == b
+
+
+def test_fused_p1_model():
+    """With P1 in the A1 epilogue as well, the forward keeps two stages."""
+    info = dict(nnz1=NNZ1, nnz2=NNZ2, a2_taps=1, n_taps=TAPS, a1_rot=2)
+    both = bench.stage_model(G, info, 1, "fp32", fused=True, fused_p1=True)
+    plain = bench.stage_model(G, info, 1, "fp32")
+    assert [s and s[0] for s in both["fwd"]] == ["spmm1", None, "spmm2", None]
+    assert both["adj"] == bench.stage_model(G, info, 1, "fp32", fused=True)["adj"]
+    assert both["fwd"][0] == plain["fwd"][0] and both["fwd"][2] == plain["fwd"][2]
+    only = bench.stage_model(G, info, 1, "fp32", fused_p1=True)
+    assert [s and s[0] for s in only["fwd"]] == ["spmm1", None, "spmm2", "permute2"]
+    assert only["adj"] == plain["adj"]

@@ -1,8 +1,9 @@
 """The reshapes P2 (after A2) and P1^-1 (after A2^T) folded into the tile
-products' epilogues (SRT_FUSE_RESHAPES; Algorithms 1 and 2: the same sums,
-written in the next step's layout): bitwise equal to the default plan, which
-runs them as kernels of their own, through device buffers and the
-host-buffer calls, and within FP32 tolerance of the oracle."""
+products' epilogues, and P1 into the epilogue of the A1 product stored by
+rotation (SRT_FUSE_RESHAPES; Algorithms 1 and 2: the same sums, written in
+the next step's layout): bitwise equal to the default plan, which runs them
+as kernels of their own, through device buffers and the host-buffer calls,
+and within FP32 tolerance of the oracle."""
 import numpy as np
 import pytest
 
@@ -33,7 +34,17 @@ GEOMS = [
     dict(ms=8, mz=12, dxy=0.5, dz=0.4, radius=6.0, n_phi=260, n_zs=5, n_ell=17, zs=(-1.0, 1.0)),
     # 12 columns: one 128-column chunk, mostly empty
     dict(ms=10, mz=16, dxy=0.4, dz=0.25, radius=6.0, n_phi=12, n_zs=16, n_ell=30),
+    # 520 slabs: A1 (8-fold) in two blocks of 256 slabs and one of 8, odd
+    # radius count (a half-empty radius pair in A1's fused blocks)
+    dict(ms=8, mz=520, dxy=0.5, dz=0.05, radius=6.0, n_phi=8, n_zs=4, n_ell=11,
+         zs=(-0.1, 0.1)),                                  # 4 rings spaced dz
 ]
+
+
+def _fwd_launches(plan, g):
+    """P1 folds into A1 where A1 is stored by rotation and n_phi, mz are
+    multiples of 4; P2 into A2 whenever the tiles run."""
+    return 2 if plan.info["a1_rot"] > 0 and g.n_phi % 4 == 0 and g.mz % 4 == 0 else 3
 
 
 def _plans(srt, orc, sz, **kw):
@@ -49,7 +60,8 @@ def test_fused_equals_separate(srt, orc, sz, batch):
     import torch
     plan, sep, g, o = _plans(srt, orc, sz)
     assert plan.info["a2_taps"] == 1 and plan.info["tile_records"][0] > 0
-    assert plan.launches_per_call(0, batch) == 3 and plan.launches_per_call(1, batch) == 3
+    assert plan.launches_per_call(0, batch) == _fwd_launches(plan, g)
+    assert plan.launches_per_call(1, batch) == 3
     assert sep.launches_per_call(0, batch) == 4 and sep.launches_per_call(1, batch) == 4
     rng = np.random.default_rng(7)
     f = to_dev(rng.uniform(0, 1, (batch, *g.f_shape)))
@@ -57,7 +69,7 @@ def test_fused_equals_separate(srt, orc, sz, batch):
     pf, pa = plan.forward(f), plan.adjoint(y)
     assert torch.equal(pf, sep.forward(f))
     assert torch.equal(pa, sep.adjoint(y))
-    if g.n_phi <= 32:
+    if g.n_phi <= 32 and g.mz <= 32:
         assert rel_l2(to_np(pf[-1]), orc.forward(o, to_np(f)[-1])) <= FP32_TOL
         assert rel_l2(to_np(pa[0]), orc.adjoint(o, to_np(y)[0])) <= FP32_TOL
     plan.close()
@@ -95,5 +107,21 @@ def test_unfused_when_width_not_multiple_of_4(srt, orc):
     f = to_dev(rng.uniform(0, 1, (1, *g.f_shape)))
     assert torch.equal(plan.forward(f), sep.forward(f))
     assert rel_l2(to_np(plan.forward(f)[0]), orc.forward(o, to_np(f)[0])) <= FP32_TOL
+    plan.close()
+    sep.close()
+
+
+@pytest.mark.parametrize("sz", [GEOMS[0], GEOMS[2], GEOMS[4]])
+@pytest.mark.parametrize("batch", [1, 3])
+def test_fused_p1_with_rowwise_products(srt, orc, sz, batch):
+    """Row-per-warp products (A1 by quarter turns, no register tiles): only
+    P1 folds, into A1; the forward makes 3 launches, the adjoint 4."""
+    import torch
+    plan, sep, g, o = _plans(srt, orc, sz, rowwise=True)
+    assert plan.info["a1_rot"] == 1 and plan.info["tile_records"][0] == 0
+    assert plan.launches_per_call(0, batch) == 3 and plan.launches_per_call(1, batch) == 4
+    rng = np.random.default_rng(10)
+    f = to_dev(rng.uniform(0, 1, (batch, *g.f_shape)))
+    assert torch.equal(plan.forward(f), sep.forward(f))
     plan.close()
     sep.close()

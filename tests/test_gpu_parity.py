@@ -391,9 +391,10 @@ def test_plan_info_and_timing(srt, orc):
     with pytest.raises(SrtError):
         plan.stage_times(1)
     assert plan.launches_per_call(0) == 4 and plan.launches_per_call(1) == 4
-    # A2 / A2^T tiles writing the reshaped layouts themselves: 3 launches
+    # A2 / A2^T tiles writing the reshaped layouts themselves, and A1 (8-fold)
+    # writing Y1': 2 launches forward, 3 adjoint
     s = srt.Plan(g.with_(fuse_reshapes=True))
-    assert s.launches_per_call(0) == 3 and s.launches_per_call(1) == 3
+    assert s.launches_per_call(0) == 2 and s.launches_per_call(1) == 3
     assert inf["a2_taps"] == 1  # rings at the slab centres: A2 from the taps
     c = srt.Plan(g.with_(csr_only=True))
     assert c.info["a2_taps"] == 0 and c.info["n_taps"] == 0
