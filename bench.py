@@ -56,6 +56,8 @@ def parse():
                    help="piecewise-linear intermediate in rho (else constant on the radius bins)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=100)
+    p.add_argument("--e2e-depth", type=int, default=3,
+                   help="steps submitted ahead of the one whose result is read (1-3)")
     return p.parse_args()
 
 
@@ -484,44 +486,56 @@ def run_ours(args):
             _ = float(p_h[0, 0, 0, 0]) + float(a_h[0, 0, 0, 0])
         serial_s = reduce_max(time.perf_counter() - t0, world)
         # pipelined (srt_pipe_*): a call's input copy overlaps the earlier
-        # calls' computation; every step's result is read on the host
+        # calls' computation; every step's result is read on the host, `depth`
+        # steps after it was submitted
+        depth = min(3, max(1, args.e2e_depth))  # the pipe keeps the last 8 calls' events
         pipe = Pipeline(plan, B, slots=3)
-        p2 = [p_h, torch.empty_like(p_h).pin_memory()]
-        a2 = [a_h, torch.empty_like(a_h).pin_memory()]
+        nbuf = depth + 1
+        p2 = [p_h] + [torch.empty_like(p_h).pin_memory() for _ in range(depth)]
+        a2 = [a_h] + [torch.empty_like(a_h).pin_memory() for _ in range(depth)]
+        times = []  # each call's copies, transform and compute-stream idle time
 
         def submit(k):
-            return (pipe.submit("forward", f_h, p2[k % 2]), pipe.submit("adjoint", y_h, a2[k % 2]))
+            return (pipe.submit("forward", f_h, p2[k % nbuf]),
+                    pipe.submit("adjoint", y_h, a2[k % nbuf]))
 
         def read(k, tickets):
             for t in tickets:
                 pipe.wait(t)
-            return float(p2[k % 2][0, 0, 0, 0]) + float(a2[k % 2][0, 0, 0, 0])
+            v = float(p2[k % nbuf][0, 0, 0, 0]) + float(a2[k % nbuf][0, 0, 0, 0])
+            times.extend(pipe.stage_times(t) for t in tickets)
+            return v
 
         read(1, submit(1))
         read(0, submit(0))
+        times.clear()
         barrier(world)
         t0 = time.perf_counter()
-        prev = None
+        queue = []
         for k in range(args.e2e_steps):
-            cur = submit(k)
-            if prev is not None:
-                read(k - 1, prev)
-            prev = cur
-        read(args.e2e_steps - 1, prev)
+            queue.append((k, submit(k)))
+            if len(queue) > depth:
+                read(*queue.pop(0))
+        while queue:
+            read(*queue.pop(0))
         e2e_s = reduce_max(time.perf_counter() - t0, world)
-        # the pipe's own events for its last calls: copies, transform, and
-        # the compute stream's idle time before each transform
-        last = prev[-1]
-        st = [pipe.stage_times(t) for t in range(max(0, last - 7), last + 1)]
-        pipe_ms = {k: round(float(np.mean([x[i] for x in st])), 3)
-                   for i, k in enumerate(("h2d", "transform", "d2h", "compute_idle"))}
+        names = ("h2d", "transform", "d2h", "compute_idle")
+        # the pipe's own events: copies, transform, and the compute stream's
+        # idle time before each transform, over the last 8 calls and all
+        pipe_ms = {k: round(float(np.mean([x[i] for x in times[-8:]])), 3)
+                   for i, k in enumerate(names)}
+        pipe_all = {k: round(float(np.mean([x[i] for x in times])), 3)
+                    for i, k in enumerate(names)}
+        pipe_all["compute_idle_total_ms"] = round(float(np.sum([x[3] for x in times])), 2)
         pipe.close()
         e2e = {"value": world * args.e2e_steps * B / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": f_h.numel() * 4 + y_h.numel() * 4,
                "d2h_bytes_per_step": p_h.numel() * 4 + a_h.numel() * 4,
                "steps": args.e2e_steps,
                "api": "srt_pipe_submit / srt_pipe_wait, 3 slots (calls in flight)",
+               "depth": depth,
                "pipe_ms_per_call_last8": pipe_ms,
+               "pipe_ms_per_call_all": pipe_all,
                "one_call_at_a_time": world * args.e2e_steps * B / serial_s}
 
     launches = args.steps * (plan.launches_per_call(0, B) + plan.launches_per_call(1, B))

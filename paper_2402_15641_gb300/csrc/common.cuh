@@ -363,6 +363,16 @@ __device__ __forceinline__ float4 srt_ldg_keep(const float* p) {
   return r;
 }
 
+// The L2 lines holding bytes [b, e), requested by a warp's 32 lanes at once
+// (one line each per round): a list of sparse records read in order then
+// costs one L2-miss latency instead of one per line.
+__device__ __forceinline__ void srt_prefetch_l2(const void* b, const void* e) {
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(b) & ~(uintptr_t)127;
+  const uintptr_t hi = reinterpret_cast<uintptr_t>(e);
+  for (uintptr_t p = lo + (threadIdx.x & 31) * 128; p < hi; p += 32 * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ float srt_bf16_to_f32(uint16_t v) {
   return __uint_as_float(((uint32_t)v) << 16);
 }
