@@ -22,7 +22,7 @@ def srt():
     build.build()
     return S
 
-FP32_TOL = 1e-5
+FP32_TOL, BF16_TOL = 1e-5, 5e-3
 
 GEOMS = [
     dict(I.sizes("srt32")),
@@ -56,9 +56,10 @@ def _plans(srt, orc, sz, **kw):
 
 @pytest.mark.parametrize("sz", GEOMS)
 @pytest.mark.parametrize("batch", [1, 2])
-def test_fused_equals_separate(srt, orc, sz, batch):
+@pytest.mark.parametrize("wdt", ["fp32", "bf16"])
+def test_fused_equals_separate(srt, orc, sz, batch, wdt):
     import torch
-    plan, sep, g, o = _plans(srt, orc, sz)
+    plan, sep, g, o = _plans(srt, orc, sz, weight_dtype=wdt)
     assert plan.info["a2_taps"] == 1 and plan.info["tile_records"][0] > 0
     assert plan.launches_per_call(0, batch) == _fwd_launches(plan, g)
     assert plan.launches_per_call(1, batch) == 3
@@ -70,8 +71,9 @@ def test_fused_equals_separate(srt, orc, sz, batch):
     assert torch.equal(pf, sep.forward(f))
     assert torch.equal(pa, sep.adjoint(y))
     if g.n_phi <= 32 and g.mz <= 32:
-        assert rel_l2(to_np(pf[-1]), orc.forward(o, to_np(f)[-1])) <= FP32_TOL
-        assert rel_l2(to_np(pa[0]), orc.adjoint(o, to_np(y)[0])) <= FP32_TOL
+        tol = FP32_TOL if wdt == "fp32" else BF16_TOL
+        assert rel_l2(to_np(pf[-1]), orc.forward(o, to_np(f)[-1])) <= tol
+        assert rel_l2(to_np(pa[0]), orc.adjoint(o, to_np(y)[0])) <= tol
     plan.close()
     sep.close()
 
