@@ -16,6 +16,8 @@
 // rot^s(p).  Mode 2 (A1^T): output row p walks, for s = 0..3, stored row
 // rot^-s(p) of the stored transpose and gathers row (j + s n_phi/4, l): the
 // same terms in the same order (ascending j, then l) as the full transpose.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace {
@@ -95,6 +97,7 @@ struct Rows {
   uint64_t magic;  // ceil(2^40 / rot.ms)
   int xrows;       // rows of the gathered operand (debug-build checks)
   int64_t ldn;     // > 0: reshape P1 fused (k_spmm_rot), stride of Y1''s rows
+  int pack16;      // BF16 entries of A1 by rotation, pixels < 2^16 (k_spmm_rot PK)
 };
 
 // Stored row and gathered-row remap of segment s of output row `row`.
@@ -190,7 +193,12 @@ __global__ void __launch_bounds__(256) k_spmm_plain(int rows, const int32_t* __r
 // the reshape P1 in the epilogue.  The block's 8 rows go through shared
 // memory, 128 slabs at a time, and are written as Y1'[(l, k)][b G + j],
 // row stride ldn, 16 bytes (4 sensor columns) per radius and slab.
-template <typename V, int CH, int MODE, bool TR>
+// PK (BF16 entries, MODE 1, fewer than 2^16 pixels): each lane packs its
+// entry's turned pixel and BF16 value into one word, so the warp broadcasts
+// an entry with one shuffle instead of two (same pixel, same value; the
+// shuffles share the L1 data pipe with the gathers: A1 1.580 -> 1.506 ms
+// at 256^3 with BF16 entries).
+template <typename V, int CH, int MODE, bool TR, bool PK>
 __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
                                                   const int32_t* __restrict__ rowptr,
                                                   const int32_t* __restrict__ col,
@@ -232,17 +240,29 @@ __global__ void __launch_bounds__(256) k_spmm_rot(int rows, int r0,
     for (int eb = e0; eb < e1; eb += 32) {
       int c = 0;
       float v = 0.f;
+      uint32_t pw = 0;
       if (eb + lane < e1) {
         c = col[eb + lane];
         c = MODE == 1 ? rot_pixel(c, t, ms, magic, mir) : c + off;
         SRT_CHECK_GATHER(0, c, xrows, g_viol);
-        v = wval<V>(val[eb + lane]);
+        if constexpr (PK)
+          pw = ((uint32_t)c << 16) | (uint32_t)val[eb + lane];
+        else
+          v = wval<V>(val[eb + lane]);
       }
       const int cnt = min(32, e1 - eb);
 #pragma unroll 1
       for (int i = 0; i < cnt; ++i) {  // not unrolled, as in k_spmm_plain
-        const int ci = __shfl_sync(FULL, c, i);
-        const float vi = __shfl_sync(FULL, v, i);
+        int ci;
+        float vi;
+        if constexpr (PK) {
+          const uint32_t wi = __shfl_sync(FULL, pw, i);
+          ci = (int)(wi >> 16);
+          vi = __uint_as_float(wi << 16);
+        } else {
+          ci = __shfl_sync(FULL, c, i);
+          vi = __shfl_sync(FULL, v, i);
+        }
         const float* xr = x + (int64_t)ci * ldx;
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
@@ -370,18 +390,27 @@ int launch(const SrtCsr& A, const V* val, const Rows& W, const float* x, int64_t
     const int CH = chunks >= 2 ? 2 : chunks;
     dim3 grid(gx, (ncols + 128 * CH - 1) / (128 * CH), batch);
     const SrtRot& r = W.rot;
-#define SRT_ROT_LAUNCH(C, T)                                                                  \
-  k_spmm_rot<V, C, MODE, T><<<grid, block, 0, st>>>(W.rows, W.r0, A.rowptr, A.col, val, x,   \
-                                                    ldx, bsx, y, ldy, bsy, ncols, W.G, W.R,   \
-                                                    W.TG, W.S, r.ms, r.n_ell, r.q, r.mirror,  \
-                                                    W.magic, W.xrows, W.ldn)
-    if (MODE == 1 && W.ldn > 0) {
-      if (CH == 2) SRT_ROT_LAUNCH(2, MODE == 1);
-      else SRT_ROT_LAUNCH(1, MODE == 1);
+#define SRT_ROT_LAUNCH(C, T, P)                                                                 \
+  k_spmm_rot<V, C, MODE, T, P><<<grid, block, 0, st>>>(W.rows, W.r0, A.rowptr, A.col, val, x,  \
+                                                       ldx, bsx, y, ldy, bsy, ncols, W.G, W.R,  \
+                                                       W.TG, W.S, r.ms, r.n_ell, r.q,           \
+                                                       r.mirror, W.magic, W.xrows, W.ldn)
+    constexpr bool kPk = MODE == 1 && std::is_same<V, uint16_t>::value;
+    constexpr bool kTr = MODE == 1;
+    const bool tr = kTr && W.ldn > 0, pk = kPk && W.pack16;
+    if (tr && pk) {
+      if (CH == 2) SRT_ROT_LAUNCH(2, kTr, kPk);
+      else SRT_ROT_LAUNCH(1, kTr, kPk);
+    } else if (tr) {
+      if (CH == 2) SRT_ROT_LAUNCH(2, kTr, false);
+      else SRT_ROT_LAUNCH(1, kTr, false);
+    } else if (pk) {
+      if (CH == 2) SRT_ROT_LAUNCH(2, false, kPk);
+      else SRT_ROT_LAUNCH(1, false, kPk);
     } else if (CH == 2) {
-      SRT_ROT_LAUNCH(2, false);
+      SRT_ROT_LAUNCH(2, false, false);
     } else {
-      SRT_ROT_LAUNCH(1, false);
+      SRT_ROT_LAUNCH(1, false, false);
     }
 #undef SRT_ROT_LAUNCH
   } else {
@@ -434,7 +463,10 @@ int srt_spmm(const SrtCsr& A, int wdt, const float* x, int64_t ldx, int64_t bsx,
     TG = 4;
     S = 0;
   }
-  const Rows W{(int)rows, (int)r0, G, R, TG, S, rot, magic, srt_checked_rows(xr), ldn};
+  // BF16 entries of A1 turned onto fewer than 2^16 pixels: pixel and value
+  // in one 32-bit word (one shuffle per entry)
+  const int pack16 = rot.mode == 1 && wdt == SRT_BF16 && A.cols <= 65536;
+  const Rows W{(int)rows, (int)r0, G, R, TG, S, rot, magic, srt_checked_rows(xr), ldn, pack16};
   if (wdt == SRT_BF16) return dispatch<uint16_t>(A, A.v16, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
   return dispatch<float>(A, A.v32, W, x, ldx, bsx, y, ldy, bsy, ncols, batch, st);
 }
